@@ -1,0 +1,223 @@
+"""FP64 CPU oracle for the image-plane chi^2 path (test infrastructure only).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (the CUDA library and its
+binding) never does: it shares no code with this oracle.
+
+The C++ source ``lt_oracle.cpp`` is compiled with ``-ffp-contract=off`` so
+every floating-point operation is a separately rounded IEEE double, on x86
+and Arm alike.  See that file for the step-by-step statement of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lt_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "liblt_oracle.so")
+
+PARAM_ROWS = ("kind", "x", "y", "e", "phi", "r_core", "r_cut", "sigma_v")
+GRAD_ROWS = ("x", "y", "e", "phi", "r_core", "sigma_v")
+
+
+class Hit(C.Structure):
+    _fields_ = [("src", C.c_int32), ("undecidable", C.c_int32), ("tri", C.c_int64),
+                ("x", C.c_double), ("y", C.c_double), ("w", C.c_double * 3)]
+
+
+class Pair(C.Structure):
+    _fields_ = [("src", C.c_int32), ("inside", C.c_int32), ("tri", C.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library (g++, OpenMP, no FP contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        lp = C.POINTER(C.c_int64)
+        L.lto_alpha_points.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+        L.lto_deflect_grid.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, C.c_int, C.c_int, C.c_int, dp, dp]
+        L.lto_find_images.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp,
+                                      C.c_int, C.c_int64, C.POINTER(Hit), C.c_int64,
+                                      C.POINTER(Pair), lp]
+        L.lto_find_images.restype = C.c_int64
+        L.lto_barycentres.argtypes = [dp, C.c_int, C.c_int, dp, dp, ip, C.c_int, dp, dp, dp]
+        L.lto_chi2.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                               C.c_int, C.c_int, C.c_int, dp, dp, dp, ip, C.c_int, dp,
+                               C.c_int, C.c_int64, C.POINTER(Hit), dp, lp, dp, dp, lp, lp]
+        L.lto_chi2_frozen.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, ip,
+                                      C.c_int, dp, lp, dp]
+        L.lto_chi2_grad.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, ip,
+                                    C.c_int, dp, lp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _l(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def _params(params):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    assert p.ndim == 2 and p.shape[0] == 8, "params must be [8][n_pot] for one sample"
+    return p
+
+
+def alpha_points(params, x, y):
+    """Deflection (ax, ay) and sum_k |alpha_k| at points x, y (one sample)."""
+    p, pp = _d(_params(params))
+    x, xp = _d(np.atleast_1d(x))
+    y, yp = _d(np.atleast_1d(y))
+    n = x.size
+    ax, axp = _d(np.zeros(n))
+    ay, ayp = _d(np.zeros(n))
+    s, sp = _d(np.zeros(n))
+    lib().lto_alpha_points(pp, p.shape[1], n, xp, yp, axp, ayp, sp)
+    return ax, ay, s
+
+
+def deflect_grid(params, grid, n_threads: int = 1):
+    """alpha over a grid (x0, y0, dx, dy, nx, ny): [ny][nx][2] and sum|alpha_k|."""
+    x0, y0, dx, dy, nx, ny = grid
+    p, pp = _d(_params(params))
+    out, op = _d(np.zeros((ny, nx, 2)))
+    s, sp = _d(np.zeros((ny, nx)))
+    lib().lto_deflect_grid(pp, p.shape[1], x0, y0, dx, dy, nx, ny, n_threads, op, sp)
+    return out, s
+
+
+def find_images(params, grid, src_xy, dls_ds, d_src=None, n_threads: int = 1,
+                capacity: int = 1 << 16, und_capacity: int = 1 << 12):
+    """Hits (list of dict) and undecidable pairs for explicit source positions."""
+    x0, y0, dx, dy, nx, ny = grid
+    p, pp = _d(_params(params))
+    src, sp = _d(np.asarray(src_xy, dtype=np.float64).reshape(-1, 2))
+    r, rp = _d(np.atleast_1d(dls_ds))
+    n_src = src.shape[0]
+    if d_src is None:
+        d_src = np.zeros(n_src)
+    ds, dsp = _d(d_src)
+    hits = (Hit * capacity)()
+    und = (Pair * und_capacity)()
+    n_und = C.c_int64(0)
+    n = lib().lto_find_images(pp, p.shape[1], x0, y0, dx, dy, nx, ny, n_src, sp, rp, dsp,
+                              n_threads, capacity, hits, und_capacity, und, C.byref(n_und))
+    if n > capacity:
+        raise RuntimeError(f"oracle hit capacity {capacity} < {n}")
+    H = [dict(src=h.src, tri=h.tri, x=h.x, y=h.y, w=tuple(h.w), undecidable=h.undecidable)
+         for h in hits[:n]]
+    U = [dict(src=u.src, tri=u.tri, inside=u.inside) for u in und[:min(n_und.value, und_capacity)]]
+    return H, U
+
+
+def barycentres(params, obs):
+    """Per-system barycentres [n_sys][2] and their FP64 uncertainty [n_sys]."""
+    p, pp = _d(_params(params))
+    ox, oxp = _d(obs["x"])
+    oy, oyp = _d(obs["y"])
+    osys, osp = _i(obs["sys"])
+    r, rp = _d(obs["dls_ds"])
+    n_sys = r.size
+    b, bp = _d(np.zeros((n_sys, 2)))
+    d, dpp = _d(np.zeros(n_sys))
+    lib().lto_barycentres(pp, p.shape[1], ox.size, oxp, oyp, osp, n_sys, rp, bp, dpp)
+    return b, d
+
+
+def chi2(params, grid, obs, n_threads: int = 1, capacity: int = 1 << 16):
+    """Full chi^2 of Eq. 8 for one sample; returns a dict of all intermediates."""
+    x0, y0, dx, dy, nx, ny = grid
+    p, pp = _d(_params(params))
+    ox, oxp = _d(obs["x"])
+    oy, oyp = _d(obs["y"])
+    sg, sgp = _d(obs["sigma"])
+    osys, osp = _i(obs["sys"])
+    r, rp = _d(obs["dls_ds"])
+    n_obs, n_sys = ox.size, r.size
+    hits = (Hit * capacity)()
+    c2 = C.c_double(0.0)
+    mt, mtp = _l(np.zeros(n_obs))
+    mxy, mxyp = _d(np.zeros((n_obs, 2)))
+    b, bp = _d(np.zeros((n_sys, 2)))
+    nh = C.c_int64(0)
+    nu = C.c_int64(0)
+    rc = lib().lto_chi2(pp, p.shape[1], x0, y0, dx, dy, nx, ny, n_obs, oxp, oyp, sgp, osp,
+                        n_sys, rp, n_threads, capacity, hits, C.byref(c2), mtp, mxyp, bp,
+                        C.byref(nh), C.byref(nu))
+    if rc != 0:
+        raise RuntimeError(f"oracle hit capacity {capacity} < {nh.value}")
+    H = [dict(src=h.src, tri=h.tri, x=h.x, y=h.y, w=tuple(h.w), undecidable=h.undecidable)
+         for h in hits[:nh.value]]
+    return dict(chi2=c2.value, match_tri=mt.copy(), match_xy=mxy.copy(), bary=b.copy(),
+                hits=H, n_undecidable=nu.value)
+
+
+def chi2_frozen(params, grid, obs, match_tri):
+    """chi^2 with the triangle assignment held fixed (value only)."""
+    x0, y0, dx, dy, nx, ny = grid
+    p, pp = _d(_params(params))
+    ox, oxp = _d(obs["x"])
+    oy, oyp = _d(obs["y"])
+    sg, sgp = _d(obs["sigma"])
+    osys, osp = _i(obs["sys"])
+    r, rp = _d(obs["dls_ds"])
+    mt, mtp = _l(match_tri)
+    c2 = C.c_double(0.0)
+    lib().lto_chi2_frozen(pp, p.shape[1], x0, y0, dx, dy, nx, ny, ox.size, oxp, oyp, sgp,
+                          osp, r.size, rp, mtp, C.byref(c2))
+    return c2.value
+
+
+def chi2_grad(params, grid, obs, match_tri):
+    """(chi^2, d chi^2/d params [n_pot][6]) with the assignment held fixed."""
+    x0, y0, dx, dy, nx, ny = grid
+    p, pp = _d(_params(params))
+    ox, oxp = _d(obs["x"])
+    oy, oyp = _d(obs["y"])
+    sg, sgp = _d(obs["sigma"])
+    osys, osp = _i(obs["sys"])
+    r, rp = _d(obs["dls_ds"])
+    mt, mtp = _l(match_tri)
+    c2 = C.c_double(0.0)
+    g, gp = _d(np.zeros((p.shape[1], 6)))
+    lib().lto_chi2_grad(pp, p.shape[1], x0, y0, dx, dy, nx, ny, ox.size, oxp, oyp, sgp, osp,
+                        r.size, rp, mtp, C.byref(c2), gp)
+    return c2.value, g
