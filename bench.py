@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the image-plane chi^2 path on one GB300 (or N, one process each).
+
+Workload (one step = one chi^2 evaluation of one lens-parameter sample):
+  100 PIEMD potentials (centres in a 200" square, e U[0,0.5], r_core
+  0.05-1", r_cut 50-200", sigma_v log-U[50,1200] km/s), 2000^2 image-plane
+  grid over 200", 20 multiple-image systems (72 observed images, stored in
+  tests/golden/obs_c2.json), mixed precision; the FP64 form is timed beside it.
+
+Metric: chi^2 evaluations/s (whole job) and node x potential deflections/s.
+Each rank evaluates its own samples (independent MCMC proposals): weak
+scaling, no collective on the data path (a barrier and a max-reduction of the
+timings only).
+
+--impl reference runs the FP64 CPU oracle on the host cores instead (rank 0),
+on a bounded band of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "chi² evals/s & node·potential deflections/s, mixed vs FP64 on one GB300"
+UNIT = "chi2_evals/s"
+WORKLOAD = ("c2: 100 PIEMD, 2000^2 grid over 200\", 20 systems / 72 observed images, "
+            "one lens sample per chi^2 evaluation")
+SM_PER_GPU_FALLBACK = 152
+# Algorithmic work of one PIEMD node x potential evaluation (difference form):
+# 64 FP32 pipe operations and 8 MUFU operations; at 128 FP32 lanes and 16
+# MUFU lanes per SM per clock both pipes allow 2 node x potential per SM-clock.
+PIEMD_NODE_POT_PER_SM_CLK = 2.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_obs():
+    with open(os.path.join(ROOT, "tests", "golden", "obs_c2.json")) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def traffic_for(kernel: str, source: str):
+    """DRAM traffic per launch recorded in profiles/<kernel>_*.md, if the kernel
+    source has not changed since the capture (else None)."""
+    src_path = os.path.join(ROOT, "paper_1902_03252_gb300", "csrc", source)
+    with open(src_path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if not (name.startswith(kernel) and name.endswith(".md")):
+            continue
+        with open(os.path.join(pdir, name)) as f:
+            txt = f.read()
+        m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        m2 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+        if m1 and m2 and m2.group(1) == sha:
+            return float(m1.group(1))
+    return None
+
+
+def cpu_baseline_oracle(w, o, seconds_hint=15.0):
+    """One full chi^2 evaluation of the workload by the FP64 oracle."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = oracle.chi2(w.params[0], w.grids[0].as_tuple(), o, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "one full chi^2 evaluation of the workload (deflection on all cores, "
+                      "triangle search single-threaded)",
+            "seconds": dt, "chi2": res["chi2"]}
+
+
+# --------------------------------------------------------------- reference
+def run_reference(a, rank, world):
+    """The FP64 oracle on the host cores, each step a band of grid rows."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1902_03252_gb300 import workloads as W
+    oracle.build()
+    w = W.c2()
+    o = load_obs()
+    p = w.params[0]
+    g = w.grids[0]
+    threads = os.cpu_count() or 1
+    bary, _ = oracle.barycentres(p, o)
+
+    def band(rows):
+        sub = (g.x0, g.y0, g.dx, g.dy, g.nx, rows + 1)
+        t0 = time.perf_counter()
+        oracle.find_images(p, sub, bary, o["dls_ds"], n_threads=threads, capacity=1 << 16)
+        return time.perf_counter() - t0
+
+    # size the band so that warm-up + steps take about two minutes
+    probe_rows = 20
+    t_probe = band(probe_rows)
+    per_row = t_probe / probe_rows
+    budget = 120.0 / max(1, a.steps + a.warmup)
+    rows = int(min(g.ny - 1, max(10, budget / per_row)))
+    for _ in range(a.warmup):
+        band(rows)
+    times = [band(rows) for _ in range(a.steps)]
+    frac = rows / (g.ny - 1)
+    t = statistics.mean(times)
+    value = frac / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{rows} of {g.ny - 1} cell rows per step (deflection and "
+                                   "triangle search of that band), scaled to whole evaluations"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(a, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1902_03252_gb300 import _build, lt, workloads as W
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = W.c2()
+    o = load_obs()
+    grid = [w.grids[0].as_tuple()]
+    nodes = w.grids[0].nodes
+    node_pot = nodes * w.n_pot
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    obs = lt.Observations.from_dict(o, device=dev)
+    shape = None if a.no_autotune else m.autotune(grid[0])
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    # correctness of the timed configuration
+    m.chi2(grid, obs, precision=lt.MIXED, out=out)
+    st, stats = m.sync()
+    if st != lt.LT_OK:
+        raise RuntimeError(f"lt status {st}")
+
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            m.chi2(grid, obs, precision=precision, out=out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        m.profile(True)
+        m.profile_read(reset=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record()
+            m.chi2(grid, obs, precision=precision, out=out)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        prof = m.profile_read(reset=True)
+        m.profile(False)
+        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        return statistics.mean(ms), ms, prof, wall
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms_mixed, ms_list, prof, wall = timed(lt.MIXED, a.steps, a.warmup)
+    clk = clocks.stop()
+    st, stats = m.sync()
+    ms_mixed = max_over_ranks(ms_mixed)
+    value = world * 1000.0 / ms_mixed
+
+    ms64, _, prof64, _ = timed(lt.FP64, max(1, min(a.steps, a.fp64_steps)), 1)
+    ms64 = max_over_ranks(ms64)
+    value64 = world * 1000.0 / ms64
+
+    # end to end through the public API with host buffers: params from pinned
+    # host memory in, chi^2 back to pinned host memory, every step
+    host_params = torch.from_numpy(np.ascontiguousarray(w.params)).pin_memory()
+    host_out = torch.empty(1, dtype=torch.float64).pin_memory()
+    for _ in range(a.warmup):
+        m.set_params(host_params.numpy())
+        m.chi2(grid, obs, precision=lt.MIXED, out=out)
+        host_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        m.set_params(host_params.numpy())
+        m.chi2(grid, obs, precision=lt.MIXED, out=out)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / a.steps)
+    st2, _ = m.sync()
+
+    # roofline of the dominant kernel (FP32 deflection), live CUDA events
+    d = prof["deflect"]
+    defl_ms = d["ms"] / max(1, d["launches"])
+    achieved = node_pot / (defl_ms * 1e-3) / 1e9  # G node.pot / s
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = sm_count * f_max * PIEMD_NODE_POT_PER_SM_CLK / 1e9
+    traffic = traffic_for("k_deflect32", "lt_fp32.cu")
+    d64 = prof64["deflect"]
+    defl64_ms = d64["ms"] / max(1, d64["launches"])
+    launches_per_step = sum(prof[k]["launches"] for k in prof) / a.steps
+    # k_bary_obs and k_bary_sys share one timing bracket: count both
+    launches_per_step += 1
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 predicate fallback, f64 chi2)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "mixed",
+                   "l2": "flushed between timed steps (256 MB write outside the step events)",
+                   "deflect_shape": shape},
+        "node_pot_per_s": value * node_pot,
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64,
+                 "node_pot_per_s": value64 * node_pot,
+                 "deflect_kernel_ms": defl64_ms},
+        "mixed_over_fp64": value / value64,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gnode_pot/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_deflect32", "kernel_ms": defl_ms,
+                     "peak_basis": f"{sm_count} SMs x {f_max / 1e6:.0f} MHz (max SM clock) x "
+                                   "2 PIEMD node.pot per SM-clock (128 FP32 / 64 ops, "
+                                   "16 MUFU / 8 ops)"},
+        "kernel_ms_per_step": {k: prof[k]["ms"] / a.steps for k in prof},
+        "stats": stats,
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,
+                "h2d_bytes_per_step": int(host_params.numel() * 8),
+                "d2h_bytes_per_step": int(host_out.numel() * 8), "ms_per_step": e2e_ms},
+        "clocks": clk,
+        "gpu_launches": int(round(launches_per_step * a.steps)),
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(w, o)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

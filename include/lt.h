@@ -1,0 +1,239 @@
+/*
+ * lt.h -- C ABI of the GB300 (sm_103a) image-plane chi^2 library for
+ * LENSTOOL-style parametric strong-lens modelling.
+ *
+ * Method: Rexroth, Schaefer, Fourestey & Kneib (2019), "High Performance
+ * Computing for gravitational lens modeling: single vs double precision on
+ * GPUs and CPUs".  For each lens-parameter sample the library
+ *   - sums the scaled deflection of all potentials at every node of an
+ *     image-plane grid (Sect. 2.2.2, Algorithm 1 and its superposition),
+ *   - maps nodes to the source plane, beta = theta - (D_ls/D_s) alpha
+ *     (Eq. 11),
+ *   - splits every cell into two triangles and tests each mapped triangle
+ *     for containing each source / system barycentre (Sect. 2.2.2, Fig. 1),
+ *   - interpolates predicted image positions by barycentric weights,
+ *   - reduces chi^2 = sum_ij |x_obs,ij - x_ij|^2 / sigma_ij^2 (Eq. 8),
+ *   - and differentiates chi^2 w.r.t. the lens parameters with the triangle
+ *     assignment held fixed.
+ *
+ * Conventions shared by every call
+ *   Angles in arcsec, velocity dispersions in km/s, position angles in rad.
+ *   Node (i, j) of an lt_grid sits at (x0 + i*dx, y0 + j*dy).
+ *   Cell (i, j) with corners v00, v10, v01, v11 has triangles
+ *   T0 = (v00, v10, v11) and T1 = (v00, v11, v01); tri = 2*(j*(nx-1)+i) + t.
+ *   A point on a shared edge belongs to the triangle whose edge, traversed
+ *   counter-clockwise in the source plane, has dy > 0 (or dy == 0, dx < 0);
+ *   a mapped triangle with zero FP64 determinant is skipped.
+ *   Buffers marked "device" are CUDA device pointers (e.g. from torch);
+ *   "host" buffers are ordinary host memory.  The caller owns every buffer
+ *   it passes.  Streams are cudaStream_t values cast to uintptr_t (0 = the
+ *   legacy default stream).  All compute calls are stream-ordered and
+ *   asynchronous: the returned status covers argument and launch errors;
+ *   errors detected on the device (hit overflow, non-finite or invalid
+ *   parameters) are latched in the model and returned by lt_model_sync.
+ *   A model is not thread-safe; use one model per host thread.
+ */
+#ifndef LT_H
+#define LT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LT_OK = 0,
+  LT_ERR_INVALID_ARG = 1, /* bad pointer, size, grid or enum */
+  LT_ERR_CUDA = 2,        /* a CUDA runtime call failed (see lt_last_error) */
+  LT_ERR_NOMEM = 3,       /* device allocation failed */
+  LT_ERR_OVERFLOW = 4,    /* more hits / FP64 work items than capacity */
+  LT_ERR_TIMEOUT = 5,     /* reserved: no kernel of this library spin-waits */
+  LT_ERR_NONFINITE = 6    /* non-finite or out-of-domain lens parameter */
+} lt_status;
+
+typedef enum { LT_SIS = 0, LT_PIEMD = 1, LT_SIE = 2 } lt_kind;
+
+/* LT_PREC_FP64: deflection, mapping and predicate in FP64 throughout.
+ * LT_PREC_MIXED: deflection, mapping and triangle test in FP32 with a
+ * per-node running error bound; a (triangle, source) pair whose FP32
+ * orientation signs are not certain under that bound, and a hit whose FP32
+ * position bound exceeds LT_POS_TOL, are re-evaluated in FP64 with the three
+ * vertex deflections recomputed in FP64.  Image sets equal the FP64 ones. */
+typedef enum { LT_PREC_FP64 = 0, LT_PREC_MIXED = 1 } lt_precision;
+
+/* Position tolerance (arcsec) that an FP32 interpolated image must provably
+ * meet; otherwise the hit is re-interpolated in FP64. */
+#define LT_POS_TOL 2.5e-5
+
+/* Parameter rows of the params array (see lt_model_set_params). */
+enum { LT_ROW_KIND = 0, LT_ROW_X, LT_ROW_Y, LT_ROW_E, LT_ROW_PHI, LT_ROW_RCORE,
+       LT_ROW_RCUT, LT_ROW_SIGMA, LT_N_ROWS };
+/* Gradient columns of lt_chi2_grad's output. */
+enum { LT_GRAD_X = 0, LT_GRAD_Y, LT_GRAD_E, LT_GRAD_PHI, LT_GRAD_RCORE, LT_GRAD_SIGMA,
+       LT_N_GRAD };
+
+typedef struct {
+  double x0, y0, dx, dy; /* node (i,j) = (x0 + i*dx, y0 + j*dy) */
+  int32_t nx, ny;        /* nodes per row / column, each >= 1 */
+} lt_grid;
+
+typedef struct {
+  int32_t n_pot;        /* potentials per sample, >= 1 */
+  int32_t batch;        /* samples, >= 1 */
+  int64_t hit_capacity; /* per-sample capacity of the internal hit and FP64
+                           work lists used by lt_chi2 / lt_chi2_grad;
+                           0 selects 4096 */
+} lt_model_desc;
+
+typedef struct lt_model lt_model;
+
+/* One predicted image (lt_find_images output), 64 bytes. */
+typedef struct {
+  int32_t sample, src; /* sample index, source index */
+  int64_t tri;         /* triangle id within the sample's grid */
+  double x, y;         /* interpolated image position (arcsec) */
+  double w[3];         /* barycentric weights of the triangle's vertices */
+  int32_t fp64;        /* 1 if the containment or the position was decided
+                          in FP64 (mixed precision only) */
+  int32_t reserved;
+} lt_image;
+
+/* Observed multiple images, shared by every sample of a batch (the data an
+ * MCMC fits).  All pointers are device pointers. */
+typedef struct {
+  int32_t n_obs;        /* observed images, >= 1 */
+  int32_t n_sys;        /* multiple-image systems, >= 1 */
+  const double* x;      /* [n_obs] observed positions (arcsec) */
+  const double* y;      /* [n_obs] */
+  const double* sigma;  /* [n_obs] positional error budget sigma_ij (arcsec) */
+  const int32_t* sys;   /* [n_obs] system index in [0, n_sys) */
+  const double* dls_ds; /* [n_sys] D_ls/D_s of each system's source */
+} lt_obs;
+
+/* Counters of the last compute call, for reporting. */
+typedef struct {
+  int64_t hits;          /* predicted images found (all samples) */
+  int64_t ambiguous;     /* (triangle, source) pairs sent to the FP64 predicate */
+  int64_t refined;       /* FP32 hits re-interpolated in FP64 */
+  int64_t fp64_nodes;    /* node deflections evaluated in FP64 by those */
+  int64_t work_overflow; /* items dropped for lack of capacity (0 when OK) */
+} lt_stats;
+
+/* Create a model for `batch` samples of `n_pot` potentials.  Allocates the
+ * parameter buffers on the current CUDA device; workspaces grow on demand.
+ * Errors: LT_ERR_INVALID_ARG (null pointers, n_pot < 1, batch < 1),
+ * LT_ERR_NOMEM, LT_ERR_CUDA.  On error *out is NULL. */
+lt_status lt_model_create(const lt_model_desc* desc, lt_model** out);
+
+/* Destroy a model and free its device memory (synchronises its work). */
+void lt_model_destroy(lt_model* model);
+
+/* Text of the last error seen by this model (never NULL). */
+const char* lt_last_error(const lt_model* model);
+const char* lt_status_string(lt_status status);
+
+/* Load the lens parameters of every sample and run parameter preparation.
+ * params: float64 [batch][LT_N_ROWS][n_pot] (SoA per sample, Sect. 2.3):
+ *   kind (LT_SIS / LT_PIEMD / LT_SIE, stored as a double), x, y (arcsec),
+ *   e (PIEMD: ellipticity 1 - b/a, axis ratio q = 1 - e, 0 <= e < 1;
+ *      SIE: pseudo-ellipticity eps, 0 <= eps < 1), phi (rad, major axis
+ *   counter-clockwise from the x axis), r_core, r_cut (PIEMD only,
+ *   0 < r_core < r_cut, arcsec), sigma_v (km/s, >= 0).
+ * on_device != 0: params is a device pointer, else a host pointer (copied
+ * asynchronously; the host buffer must stay valid until the stream reaches
+ * the copy).  Invalid or non-finite values are latched as LT_ERR_NONFINITE
+ * (reported by lt_model_sync). */
+lt_status lt_model_set_params(lt_model* model, const double* params, int on_device,
+                              uintptr_t stream);
+
+/* Deflection field of one sample over one grid (Sect. 2.2.2: the gradient of
+ * the lensing potential summed over all potentials at every node).
+ * alpha_out: device, [ny][nx][2] of float (LT_PREC_MIXED) or double
+ * (LT_PREC_FP64).  err_out: optional device [ny][nx] float receiving the FP32
+ * running error bound of each node (LT_PREC_MIXED only; pass NULL
+ * otherwise).  Errors: LT_ERR_INVALID_ARG. */
+lt_status lt_deflect_grid(lt_model* model, int32_t sample, const lt_grid* grid,
+                          lt_precision precision, void* alpha_out, float* err_out,
+                          uintptr_t stream);
+
+/* Predicted images of explicit source positions (Fig. 1 relensing).
+ * grids: host [batch]; src_xy: device [batch][n_src][2]; dls_ds: device
+ * [batch][n_src]; out: device [batch][capacity] lt_image records, each
+ * sample's images sorted by (src, tri); n_out: device [batch] int64, the
+ * number of images of each sample (may exceed capacity: then only capacity
+ * records are written and LT_ERR_OVERFLOW is latched).
+ * Errors: LT_ERR_INVALID_ARG. */
+lt_status lt_find_images(lt_model* model, const lt_grid* grids, int32_t n_src,
+                         const double* src_xy, const double* dls_ds, lt_precision precision,
+                         int64_t capacity, lt_image* out, int64_t* n_out, uintptr_t stream);
+
+/* chi^2 of Eq. 8 for every sample: observed images mapped to the source
+ * plane, per-system barycentres (FP64), triangle search for each barycentre,
+ * barycentric image positions, and for each observed image the nearest
+ * predicted image of its system (ties to the lower triangle id); a system
+ * with no predicted image contributes (L_diag/sigma)^2 per observed image,
+ * L_diag the diagonal of its sample's grid.
+ * grids: host [batch]; obs: host struct of device pointers; chi2_out: device
+ * [batch] double.  Errors: LT_ERR_INVALID_ARG; overflow latched. */
+lt_status lt_chi2(lt_model* model, const lt_grid* grids, const lt_obs* obs,
+                  lt_precision precision, double* chi2_out, uintptr_t stream);
+
+/* chi^2 and its gradient w.r.t. (x, y, e, phi, r_core, sigma_v) of every
+ * potential with the triangle assignment and matching of this evaluation
+ * held fixed (hand-written adjoint; FP32 derivatives, FP64 accumulation).
+ * grad_out: device [batch][n_pot][LT_N_GRAD] double.  Derivatives that a
+ * potential kind does not depend on are 0. */
+lt_status lt_chi2_grad(lt_model* model, const lt_grid* grids, const lt_obs* obs,
+                       lt_precision precision, double* chi2_out, double* grad_out,
+                       uintptr_t stream);
+
+/* Copy the intermediates of the last lt_chi2 / lt_chi2_grad call (device
+ * pointers, any may be NULL): match_tri [batch][n_obs] int64 (-1 = none),
+ * match_xy [batch][n_obs][2], bary [batch][n_sys][2].  Errors:
+ * LT_ERR_INVALID_ARG if no chi^2 call has run. */
+lt_status lt_last_matches(lt_model* model, int64_t* match_tri, double* match_xy,
+                          double* bary, uintptr_t stream);
+
+/* Wait for the model's work on `stream`, fill *stats (may be NULL) with the
+ * counters of the last compute call, and return (then clear) the latched
+ * device status: LT_OK, LT_ERR_OVERFLOW or LT_ERR_NONFINITE. */
+lt_status lt_model_sync(lt_model* model, uintptr_t stream, lt_stats* stats);
+
+/* Capture the whole lt_chi2 sequence for these grids, observations, precision
+ * and output pointer into a CUDA graph owned by the model, and launch it on
+ * `stream`; later calls with the same arguments replay the graph.  Same
+ * results and errors as lt_chi2. */
+lt_status lt_chi2_graph(lt_model* model, const lt_grid* grids, const lt_obs* obs,
+                        lt_precision precision, double* chi2_out, uintptr_t stream);
+
+/* Autotune the FP32 deflection kernel's launch shape for this model's
+ * potential mix on a representative grid (times each candidate with CUDA
+ * events on `stream`) and keep the fastest for later calls.  *choice
+ * (optional) receives the index of the chosen variant. */
+lt_status lt_autotune(lt_model* model, const lt_grid* grid, uintptr_t stream, int32_t* choice);
+
+/* Per-kernel timing of later compute calls (off by default).  When enabled,
+ * every launch of the deflection, search, FP64-resolution and chi^2 kernels
+ * issued by lt_chi2 / lt_find_images is bracketed by CUDA events recorded
+ * on the caller's stream (not inside lt_chi2_graph).  lt_profile_read waits
+ * for the recorded events and returns the totals since the last reset. */
+typedef struct {
+  int64_t launches[4]; /* [0] deflection, [1] search, [2] FP64 resolution,
+                          [3] barycentres + chi^2 */
+  double ms[4];        /* summed event durations of those launches */
+  double node_pot[2];  /* node x potential evaluations by the deflection
+                          launches: [0] FP32, [1] FP64 */
+} lt_profile;
+lt_status lt_profile_enable(lt_model* model, int on);
+lt_status lt_profile_read(lt_model* model, lt_profile* out, int reset);
+
+/* Library version string. */
+const char* lt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LT_H */

@@ -1,0 +1,647 @@
+// FP64 kernels.  This translation unit is compiled with -fmad=false: every
+// double operation is rounded separately, in the order written, so the FP64
+// path evaluates the stated formulas exactly as an FP64 reference that follows
+// the same statement (up to the ulps of atan/atanh/sin/cos).
+//   k_prep        parameter preparation (a1): b0 = 4 pi (sigma_v/c)^2,
+//                 rotations, axis ratios; FP64 records in index order and
+//                 FP32 records grouped by kind with error-bound coefficients.
+//   k_deflect64   FP64 deflection of every node (Sect. 2.2.2, Algorithm 1).
+//   k_search64    FP64 lens mapping (Eq. 11) and exact triangle predicate.
+//   k_resolve64   FP64 re-evaluation of the pairs the FP32 filter could not
+//                 certify and of FP32 hits whose position bound is too large.
+//   k_bary_obs / k_bary_sys   barycentres of the observed systems.
+//   k_sort_hits   images of each sample in (source, triangle) order.
+//   k_chi2        nearest-image matching and the chi^2 of Eq. 8.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lt_internal.cuh"
+
+namespace lt {
+
+__device__ __forceinline__ int find_sample64(const int64_t* off, int n, int64_t item) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------- preparation
+constexpr int kPrepThreads = 256;
+
+__device__ __forceinline__ bool valid_params(const double* v, int* kind_out) {
+  bool ok = true;
+  for (int r = 0; r < LT_N_ROWS; ++r) ok = ok && isfinite(v[r]);
+  int kind = ok ? (int)v[LT_ROW_KIND] : -1;
+  ok = ok && (double)kind == v[LT_ROW_KIND] && kind >= 0 && kind <= 2 && v[LT_ROW_SIGMA] >= 0.0;
+  if (ok && kind != LT_SIS) ok = v[LT_ROW_E] >= 0.0 && v[LT_ROW_E] < 1.0;
+  if (ok && kind == LT_PIEMD) ok = v[LT_ROW_RCORE] > 0.0 && v[LT_ROW_RCUT] > v[LT_ROW_RCORE];
+  *kind_out = ok ? kind : LT_SIS;
+  return ok;
+}
+
+// One block per sample.  Pass 1 validates every potential and writes its
+// FP64 record (invalid ones are latched and neutralised to a zero-mass SIS);
+// pass 2 ranks potentials kind-major in index order and writes the FP32
+// record at that rank, so the FP32 kernel loops over kind segments.
+__global__ void __launch_bounds__(kPrepThreads)
+    k_prep(const double* __restrict__ params, int n_pot, Pot64* __restrict__ pot64,
+           Pot32* __restrict__ pot32, Seg32* __restrict__ seg, uint32_t* status) {
+  const int b = blockIdx.x;
+  const double* P = params + (int64_t)b * LT_N_ROWS * n_pot;
+  Pot64* p64 = pot64 + (int64_t)b * n_pot;
+  __shared__ int cnt[3];
+  __shared__ float qpart[kPrepThreads];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n_pot; k += kPrepThreads) {
+    double v[LT_N_ROWS];
+    for (int r = 0; r < LT_N_ROWS; ++r) v[r] = P[(int64_t)r * n_pot + k];
+    int kind;
+    if (!valid_params(v, &kind)) {
+      atomicOr(status, ST_NONFINITE);
+      for (int r = 0; r < LT_N_ROWS; ++r) v[r] = 0.0;
+    }
+    Pot64 p;
+    p.kind = (double)kind;
+    p.cx = v[LT_ROW_X];
+    p.cy = v[LT_ROW_Y];
+    p.c = cos(v[LT_ROW_PHI]);
+    p.s = sin(v[LT_ROW_PHI]);
+    double t = v[LT_ROW_SIGMA] / kC;
+    p.b0 = 4.0 * kPi * t * t * kArcsec;
+    p.e = v[LT_ROW_E];
+    p.q = 1.0 - p.e;
+    p.k2 = (1.0 - p.q) * (1.0 + p.q);
+    p.q2 = p.q * p.q;
+    p.a = v[LT_ROW_RCORE];
+    p.sc = v[LT_ROW_RCUT];
+    p.scale = kind == LT_PIEMD ? p.b0 * (p.sc / (p.sc - p.a)) : 0.0;
+    p.pad0 = p.pad1 = p.pad2 = 0.0;
+    p64[k] = p;
+    atomicAdd(&cnt[kind], 1);
+  }
+  __syncthreads();
+  float qsum = 0.0f;
+  for (int k = threadIdx.x; k < n_pot; k += kPrepThreads) {
+    const Pot64 p = p64[k];
+    const int kind = (int)p.kind;
+    int rank = 0;
+    for (int m = 0; m < n_pot; ++m) {
+      const int km = (int)p64[m].kind;
+      if (km < kind || (km == kind && m < k)) ++rank;
+    }
+    Pot32 f;
+    for (int w = 0; w < 5; ++w) f.f[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float cx = (float)p.cx, cy = (float)p.cy, c = (float)p.c, s = (float)p.s;
+    // First-order error-bound coefficients (units of the FP32 unit roundoff):
+    // errP0 * (4 Theta + |c|) / R-like distance covers the rounding of the
+    // node coordinates, the centre and the translation, carried through the
+    // deflection's spatial derivatives; errGx/errGy the relative rounding of
+    // the rotated-frame components; errQ the distance-proportional rounding
+    // of translation and rotation carried through the same derivatives.
+    double Q;
+    if (kind == LT_SIS) {
+      f.f[0] = make_float4(cx, cy, (float)p.b0, 0.f);
+      f.f[4] = make_float4((float)(2.0 * p.b0), 0.f, 0.f, 0.f);
+      Q = 8.0 * p.b0;
+    } else if (kind == LT_SIE) {
+      const double ge = (1.0 + p.e) / (1.0 - p.e);
+      f.f[0] = make_float4(cx, cy, c, s);
+      f.f[1] = make_float4((float)(1.0 - p.e), (float)(1.0 + p.e), (float)(p.b0 * (1.0 - p.e)),
+                           (float)(p.b0 * (1.0 + p.e)));
+      f.f[4] = make_float4((float)(4.0 * p.b0 * ge), 0.f, 0.f, 0.f);
+      Q = 16.0 * p.b0 * ge;
+    } else {
+      const double a = p.a, sc = p.sc, q2 = p.q2, q = p.q;
+      const double B = p.scale;
+      f.f[0] = make_float4(cx, cy, c, s);
+      f.f[1] = make_float4((float)q2, (float)(q2 * a * a), (float)(q2 * sc * sc), (float)p.k2);
+      f.f[2] = make_float4((float)a, (float)sc, (float)(q2 * a), (float)(q2 * sc));
+      f.f[3] = make_float4((float)(sc - a), (float)(q2 * (sc + a) * (sc - a)),
+                           (float)(q2 * (sc - a)), (float)B);
+      const double iq2 = 1.0 / q2;
+      const double gy = (14.0 + 17.0 * iq2) * (1.0 + iq2) + 10.0;
+      f.f[4] = make_float4((float)(4.0 * B / q), 80.0f, (float)gy, 0.f);
+      Q = 16.0 * B * iq2;
+    }
+    f.f[4].w = (float)Q;
+    qsum += (float)Q;
+    pot32[(int64_t)b * n_pot + rank] = f;
+  }
+  qpart[threadIdx.x] = qsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float tot = 0.0f;
+    for (int t = 0; t < kPrepThreads; ++t) tot += qpart[t];
+    seg[b] = Seg32{cnt[LT_SIS], cnt[LT_PIEMD], cnt[LT_SIE], tot};
+  }
+}
+
+cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,
+                        Seg32* seg, uint32_t* status, cudaStream_t st) {
+  k_prep<<<batch, kPrepThreads, 0, st>>>(params, n_pot, pot64, pot32, seg, status);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- FP64 deflection
+constexpr int kDefl64Threads = 128;
+constexpr int kChunk64 = 64;
+
+__global__ void __launch_bounds__(kDefl64Threads)
+    k_deflect64(const Pot64* __restrict__ pot64, int n_pot, const SampleGrid* __restrict__ grids,
+                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items,
+                double2* __restrict__ node_out) {
+  __shared__ Pot64 sp[kChunk64];
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int b = find_sample64(item_off, n_samples, item);
+    const SampleGrid g = grids[b];
+    const int64_t nodes = (int64_t)g.nx * g.ny;
+    int64_t n = (item - item_off[b]) * kDefl64Threads + threadIdx.x;
+    const bool valid = n < nodes;
+    if (!valid) n = nodes - 1;
+    const int j = (int)(n / g.nx);
+    const int i = (int)(n - (int64_t)j * g.nx);
+    const double x = g.x0 + (double)i * g.dx;
+    const double y = g.y0 + (double)j * g.dy;
+    double ax = 0.0, ay = 0.0;
+    const Pot64* pb = pot64 + (int64_t)b * n_pot;
+    for (int c0 = 0; c0 < n_pot; c0 += kChunk64) {
+      const int cn = min(kChunk64, n_pot - c0);
+      __syncthreads();
+      for (int k = threadIdx.x; k < cn; k += kDefl64Threads) sp[k] = pb[c0 + k];
+      __syncthreads();
+      for (int k = 0; k < cn; ++k) {
+        double kx, ky;
+        alpha64_one(sp[k], x, y, kx, ky);
+        ax = ax + kx;
+        ay = ay + ky;
+      }
+    }
+    if (valid) node_out[g.node_off + n] = make_double2(ax, ay);
+  }
+}
+
+cudaError_t launch_deflect64(const Pot64* pot64, int n_pot, const SampleGrid* grids,
+                             const int64_t* item_off, int n_samples, int64_t n_items,
+                             double2* node_out, int sm_count, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect64, kDefl64Threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)sm_count * per_sm;
+  if (blocks > n_items) blocks = n_items;
+  k_deflect64<<<(unsigned)blocks, kDefl64Threads, 0, st>>>(pot64, n_pot, grids, item_off,
+                                                           n_samples, n_items, node_out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ exact FP64 predicate
+// Edge function e(a, b, p) = (b - a) x (p - a), each operation rounded.
+__device__ __forceinline__ double edge64(double ax, double ay, double bx, double by, double px,
+                                         double py) {
+  double t1 = (bx - ax) * (py - ay);
+  double t2 = (by - ay) * (px - ax);
+  return t1 - t2;
+}
+__device__ __forceinline__ bool owned64(double dx, double dy) {
+  return dy > 0.0 || (dy == 0.0 && dx < 0.0);
+}
+
+// Containment of P in the mapped triangle (A, B, C): parity follows the sign
+// of the determinant, zero determinant is skipped, points on an edge belong
+// to the counter-clockwise edge with dy > 0 (or dy == 0, dx < 0).
+__device__ __forceinline__ bool in_tri64(double Ax, double Ay, double Bx, double By, double Cx,
+                                         double Cy, double Px, double Py, double w[3]) {
+  double det = edge64(Ax, Ay, Bx, By, Cx, Cy);
+  if (det == 0.0) return false;
+  double e[3] = {edge64(Ax, Ay, Bx, By, Px, Py), edge64(Bx, By, Cx, Cy, Px, Py),
+                 edge64(Cx, Cy, Ax, Ay, Px, Py)};
+  double fx[3] = {Ax, Bx, Cx}, fy[3] = {Ay, By, Cy};
+  double s = det > 0.0 ? 1.0 : -1.0;
+  for (int k = 0; k < 3; ++k) {
+    double se = s * e[k];
+    if (se > 0.0) continue;
+    if (se < 0.0) return false;
+    int k1 = k == 2 ? 0 : k + 1;
+    double dx = s > 0.0 ? fx[k1] - fx[k] : fx[k] - fx[k1];
+    double dy = s > 0.0 ? fy[k1] - fy[k] : fy[k] - fy[k1];
+    if (!owned64(dx, dy)) return false;
+  }
+  w[0] = e[1] / det;
+  w[1] = e[2] / det;
+  w[2] = e[0] / det;
+  return true;
+}
+
+__device__ __forceinline__ void append_hit(const Hit& h, Hit* hits, int64_t cap,
+                                           unsigned long long* count, uint32_t* status) {
+  unsigned long long idx = atomicAdd(count, 1ull);
+  if (idx < (unsigned long long)cap) hits[idx] = h;
+  else atomicOr(status, ST_OVERFLOW_HITS);
+}
+
+__device__ __forceinline__ void warp_append_hit64(bool flag, const Hit& h, Hit* hits,
+                                                  int64_t cap, unsigned long long* count,
+                                                  uint32_t* status) {
+  unsigned mask = __ballot_sync(0xffffffffu, flag);
+  if (!mask) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) {
+    unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+    if (idx < (unsigned long long)cap) hits[idx] = h;
+    else atomicOr(status, ST_OVERFLOW_HITS);
+  }
+}
+
+// ------------------------------------------------------------ FP64 search
+constexpr int kSearch64Threads = 128;
+
+__global__ void __launch_bounds__(kSearch64Threads)
+    k_search64(const double2* __restrict__ nodes, const SampleGrid* __restrict__ grids,
+               const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
+               Hit* __restrict__ hits, int64_t hit_cap, unsigned long long* hit_count,
+               long long* counters, uint32_t* status) {
+  long long n_hit = 0;
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int b = find_sample64(item_off, n_samples, item);
+    const SampleGrid g = grids[b];
+    const int sample = src.sample_base + b;
+    const int64_t cells = (int64_t)(g.nx - 1) * (g.ny - 1);
+    const int64_t cell = (item - item_off[b]) * kSearch64Threads + threadIdx.x;
+    const bool valid = cell < cells;
+    const int64_t cl = valid ? cell : 0;
+    const int j = (int)(cl / (g.nx - 1));
+    const int i = (int)(cl - (int64_t)j * (g.nx - 1));
+    const int64_t n00 = g.node_off + (int64_t)j * g.nx + i;
+    const double2 a00 = nodes[n00], a10 = nodes[n00 + 1], a01 = nodes[n00 + g.nx],
+                  a11 = nodes[n00 + g.nx + 1];
+    const double X0 = g.x0 + (double)i * g.dx, X1 = g.x0 + (double)(i + 1) * g.dx;
+    const double Y0 = g.y0 + (double)j * g.dy, Y1 = g.y0 + (double)(j + 1) * g.dy;
+    const double* sxy = src.xy + (int64_t)sample * src.n_src * 2;
+    const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
+    for (int k = 0; k < src.n_src; ++k) {
+      const double Px = sxy[2 * k], Py = sxy[2 * k + 1], r = sr[k];
+      // mapped vertices beta = theta - r alpha (Eq. 11)
+      const double b00x = X0 - r * a00.x, b00y = Y0 - r * a00.y;
+      const double b10x = X1 - r * a10.x, b10y = Y0 - r * a10.y;
+      const double b01x = X0 - r * a01.x, b01y = Y1 - r * a01.y;
+      const double b11x = X1 - r * a11.x, b11y = Y1 - r * a11.y;
+      // exact bounding-box rejection: a point strictly outside cannot be inside
+      const double minx = fmin(fmin(b00x, b10x), fmin(b01x, b11x));
+      const double maxx = fmax(fmax(b00x, b10x), fmax(b01x, b11x));
+      const double miny = fmin(fmin(b00y, b10y), fmin(b01y, b11y));
+      const double maxy = fmax(fmax(b00y, b10y), fmax(b01y, b11y));
+      bool cand = valid && !(Px < minx || Px > maxx || Py < miny || Py > maxy);
+      bool in0 = false, in1 = false;
+      double w0[3] = {0, 0, 0}, w1[3] = {0, 0, 0};
+      if (cand) {
+        in0 = in_tri64(b00x, b00y, b10x, b10y, b11x, b11y, Px, Py, w0);
+        in1 = in_tri64(b00x, b00y, b11x, b11y, b01x, b01y, Px, Py, w1);
+      }
+      if (__any_sync(0xffffffffu, in0 || in1)) {
+        Hit h;
+        h.src = k;
+        h.fp64 = 1;
+        h.tri = 2 * cl;
+        h.w[0] = w0[0]; h.w[1] = w0[1]; h.w[2] = w0[2];
+        h.x = w0[0] * X0 + w0[1] * X1 + w0[2] * X1;
+        h.y = w0[0] * Y0 + w0[1] * Y0 + w0[2] * Y1;
+        Hit* hb = hits + (int64_t)b * hit_cap;
+        warp_append_hit64(in0, h, hb, hit_cap, hit_count + b, status);
+        h.tri = 2 * cl + 1;
+        h.w[0] = w1[0]; h.w[1] = w1[1]; h.w[2] = w1[2];
+        h.x = w1[0] * X0 + w1[1] * X1 + w1[2] * X0;
+        h.y = w1[0] * Y0 + w1[1] * Y1 + w1[2] * Y1;
+        warp_append_hit64(in1, h, hb, hit_cap, hit_count + b, status);
+        n_hit += (int)in0 + (int)in1;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) n_hit += __shfl_xor_sync(0xffffffffu, n_hit, o);
+  if ((threadIdx.x & 31) == 0 && n_hit)
+    atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
+}
+
+cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const int64_t* item_off,
+                            int n_samples, int64_t n_items, Sources src, Hit* hits,
+                            int64_t hit_cap, unsigned long long* hit_count, long long* counters,
+                            uint32_t* status, int sm_count, cudaStream_t st) {
+  if (n_items <= 0 || src.n_src <= 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search64, kSearch64Threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)sm_count * per_sm;
+  if (blocks > n_items) blocks = n_items;
+  k_search64<<<(unsigned)blocks, kSearch64Threads, 0, st>>>(nodes, grids, item_off, n_samples,
+                                                            n_items, src, hits, hit_cap,
+                                                            hit_count, counters, status);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- FP64 point deflections
+// Deflection at up to 3 points by one warp: lanes evaluate potentials of a
+// 32-potential chunk in parallel into shared memory, then lane p sums point
+// p's contributions sequentially in potential index order.
+constexpr int kWarpsPerBlock64 = 4;
+
+__device__ void warp_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts, const double* px,
+                             const double* py, double* ax, double* ay, double2* buf /*[3][32]*/) {
+  const int lane = threadIdx.x & 31;
+  double sx = 0.0, sy = 0.0;
+  for (int c0 = 0; c0 < n_pot; c0 += 32) {
+    const int k = c0 + lane;
+    if (k < n_pot) {
+      const Pot64 p = pb[k];
+      for (int q = 0; q < npts; ++q) {
+        double kx, ky;
+        alpha64_one(p, px[q], py[q], kx, ky);
+        buf[q * 32 + lane] = make_double2(kx, ky);
+      }
+    }
+    __syncwarp();
+    if (lane < npts) {
+      const int cn = min(32, n_pot - c0);
+      for (int m = 0; m < cn; ++m) {
+        double2 v = buf[lane * 32 + m];
+        sx = sx + v.x;
+        sy = sy + v.y;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane < npts) {
+    ax[lane] = sx;
+    ay[lane] = sy;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock64)
+    k_resolve64(const Pot64* __restrict__ pot64, int n_pot, const SampleGrid* __restrict__ grids,
+                Sources src, const Work64* __restrict__ work,
+                const unsigned long long* __restrict__ work_count, int n_samples, int64_t work_cap,
+                Hit* __restrict__ hits, int64_t hit_cap, unsigned long long* hit_count,
+                long long* counters, uint32_t* status) {
+  __shared__ double2 buf[kWarpsPerBlock64][3 * 32];
+  __shared__ double res[kWarpsPerBlock64][6];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock64 + wid;
+  const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock64;
+  long long n_nodes = 0, n_hit = 0;
+  for (int64_t f = gw; f < (int64_t)n_samples * work_cap; f += nw) {
+    const int b = (int)(f / work_cap);
+    const int64_t idx = f - (int64_t)b * work_cap;
+    unsigned long long cnt = work_count[b];
+    if ((unsigned long long)idx >= cnt) {  // skip the rest of this sample quickly
+      continue;
+    }
+    const Work64 wk = work[f];
+    const SampleGrid g = grids[b];
+    const int64_t cell = wk.tri / 2;
+    const int t = (int)(wk.tri % 2);
+    const int i = (int)(cell % (g.nx - 1)), j = (int)(cell / (g.nx - 1));
+    // vertex (i, j) offsets of T0 = (00, 10, 11), T1 = (00, 11, 01)
+    const int di[3] = {0, 1, t == 0 ? 1 : 0};
+    const int dj[3] = {0, t == 0 ? 0 : 1, 1};
+    double X[3], Y[3];
+    for (int v = 0; v < 3; ++v) {
+      X[v] = g.x0 + (double)(i + di[v]) * g.dx;
+      Y[v] = g.y0 + (double)(j + dj[v]) * g.dy;
+    }
+    warp_alpha64(pot64 + (int64_t)wk.sample * n_pot, n_pot, 3, X, Y, &res[wid][0], &res[wid][3],
+                 buf[wid]);
+    n_nodes += 3;
+    bool in = false;
+    Hit h;
+    if (lane == 0) {
+      const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
+      const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
+      const double Px = sxy[2 * wk.src], Py = sxy[2 * wk.src + 1];
+      double Bx[3], By[3];
+      for (int v = 0; v < 3; ++v) {
+        Bx[v] = X[v] - r * res[wid][v];
+        By[v] = Y[v] - r * res[wid][3 + v];
+      }
+      double w[3];
+      in = in_tri64(Bx[0], By[0], Bx[1], By[1], Bx[2], By[2], Px, Py, w);
+      if (in) {
+        h.src = wk.src;
+        h.fp64 = 1;
+        h.tri = wk.tri;
+        h.w[0] = w[0]; h.w[1] = w[1]; h.w[2] = w[2];
+        h.x = w[0] * X[0] + w[1] * X[1] + w[2] * X[2];
+        h.y = w[0] * Y[0] + w[1] * Y[1] + w[2] * Y[2];
+        append_hit(h, hits + (int64_t)b * hit_cap, hit_cap, hit_count + b, status);
+        ++n_hit;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && (n_nodes || n_hit)) {
+    atomicAdd((unsigned long long*)&counters[CNT_FP64_NODES], (unsigned long long)n_nodes);
+    atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
+  }
+}
+
+cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* grids, Sources src,
+                             const Work64* work, const unsigned long long* work_count,
+                             int n_samples, int64_t work_cap, Hit* hits, int64_t hit_cap,
+                             unsigned long long* hit_count, long long* counters,
+                             uint32_t* status, int sm_count, cudaStream_t st) {
+  int blocks = sm_count * 8;
+  k_resolve64<<<blocks, 32 * kWarpsPerBlock64, 0, st>>>(pot64, n_pot, grids, src, work,
+                                                        work_count, n_samples, work_cap, hits,
+                                                        hit_cap, hit_count, counters, status);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- barycentres
+// beta_m = theta_obs,m - r_i alpha(theta_obs,m) for every (sample, observed
+// image); then each system's unweighted mean in observation order.
+__global__ void __launch_bounds__(32 * kWarpsPerBlock64)
+    k_bary_obs(const Pot64* __restrict__ pot64, int n_pot, int batch, lt_obs obs,
+               double* __restrict__ beta_obs) {
+  __shared__ double2 buf[kWarpsPerBlock64][3 * 32];
+  __shared__ double res[kWarpsPerBlock64][6];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock64 + wid;
+  const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock64;
+  for (int64_t f = gw; f < (int64_t)batch * obs.n_obs; f += nw) {
+    const int b = (int)(f / obs.n_obs);
+    const int m = (int)(f - (int64_t)b * obs.n_obs);
+    double X = obs.x[m], Y = obs.y[m];
+    warp_alpha64(pot64 + (int64_t)b * n_pot, n_pot, 1, &X, &Y, &res[wid][0], &res[wid][3],
+                 buf[wid]);
+    if (lane == 0) {
+      const double r = obs.dls_ds[obs.sys[m]];
+      beta_obs[2 * f] = X - r * res[wid][0];
+      beta_obs[2 * f + 1] = Y - r * res[wid][3];
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_bary_sys(int batch, lt_obs obs, const double* __restrict__ beta_obs,
+                           double* __restrict__ bary) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)batch * obs.n_sys) return;
+  const int b = (int)(f / obs.n_sys);
+  const int i = (int)(f - (int64_t)b * obs.n_sys);
+  double sx = 0.0, sy = 0.0;
+  int cnt = 0;
+  for (int m = 0; m < obs.n_obs; ++m) {
+    if (obs.sys[m] != i) continue;
+    sx = sx + beta_obs[2 * ((int64_t)b * obs.n_obs + m)];
+    sy = sy + beta_obs[2 * ((int64_t)b * obs.n_obs + m) + 1];
+    ++cnt;
+  }
+  bary[2 * f] = cnt ? sx / cnt : 0.0;
+  bary[2 * f + 1] = cnt ? sy / cnt : 0.0;
+}
+
+cudaError_t launch_barycentres(const Pot64* pot64, int n_pot, int batch, const lt_obs& obs,
+                               double* beta_obs, double* bary, cudaStream_t st) {
+  int64_t warps = (int64_t)batch * obs.n_obs;
+  int64_t blocks = (warps + kWarpsPerBlock64 - 1) / kWarpsPerBlock64;
+  if (blocks > 4096) blocks = 4096;
+  k_bary_obs<<<(unsigned)blocks, 32 * kWarpsPerBlock64, 0, st>>>(pot64, n_pot, batch, obs,
+                                                                 beta_obs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t n = (int64_t)batch * obs.n_sys;
+  k_bary_sys<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(batch, obs, beta_obs, bary);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ sorting
+// Write each sample's hits to lt_image records in (src, tri) order: the rank
+// of a hit is the number of hits with a smaller key (keys are unique).
+constexpr int kSortThreads = 256;
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_hits(const Hit* __restrict__ hits, const unsigned long long* __restrict__ hit_count,
+                int64_t hit_cap, int sample_base, lt_image* __restrict__ out, int64_t out_cap,
+                int64_t* __restrict__ n_out, uint32_t* status) {
+  const int b = blockIdx.x;
+  const unsigned long long total = hit_count[b];
+  const int64_t n = (int64_t)min((unsigned long long)hit_cap, total);
+  const Hit* hb = hits + (int64_t)b * hit_cap;
+  const int sample = sample_base + b;
+  if (threadIdx.x == 0) {
+    n_out[sample] = (int64_t)total;
+    if (total > (unsigned long long)out_cap) atomicOr(status, ST_OVERFLOW_HITS);
+  }
+  for (int64_t h = threadIdx.x; h < n; h += kSortThreads) {
+    const Hit me = hb[h];
+    int64_t rank = 0;
+    for (int64_t o = 0; o < n; ++o) {
+      const Hit& ot = hb[o];
+      if (ot.src < me.src || (ot.src == me.src && ot.tri < me.tri)) ++rank;
+    }
+    if (rank < out_cap) {
+      lt_image im;
+      im.sample = sample;
+      im.src = me.src;
+      im.tri = me.tri;
+      im.x = me.x;
+      im.y = me.y;
+      im.w[0] = me.w[0];
+      im.w[1] = me.w[1];
+      im.w[2] = me.w[2];
+      im.fp64 = me.fp64;
+      im.reserved = 0;
+      out[(int64_t)sample * out_cap + rank] = im;
+    }
+  }
+}
+
+cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_count, int n_samples,
+                             int64_t hit_cap, int sample_base, lt_image* out, int64_t out_cap,
+                             int64_t* n_out, uint32_t* status, cudaStream_t st) {
+  if (n_samples <= 0) return cudaSuccess;
+  k_sort_hits<<<n_samples, kSortThreads, 0, st>>>(hits, hit_count, hit_cap, sample_base, out,
+                                                  out_cap, n_out, status);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- chi^2
+// One block per sample.  Each thread takes observed images m = tid, tid+NT,
+// ..., finds the nearest predicted image of the same system (ties to the
+// lower triangle id) and adds |x_obs - x|^2/sigma^2 (or the penalty
+// (L_diag/sigma)^2 when the system has no image); the per-thread sums are
+// reduced by warp shuffles in a fixed order, then across warps.
+constexpr int kChi2Threads = 128;
+
+__global__ void __launch_bounds__(kChi2Threads)
+    k_chi2(const Hit* __restrict__ hits, const unsigned long long* __restrict__ hit_count,
+           int64_t hit_cap, int sample_base, const SampleGrid* __restrict__ grids, lt_obs obs,
+           double* __restrict__ chi2, int64_t* __restrict__ match_tri,
+           int32_t* __restrict__ match_hit, double* __restrict__ match_xy) {
+  __shared__ double wsum[kChi2Threads / 32];
+  const int b = blockIdx.x;
+  const int sample = sample_base + b;
+  const SampleGrid g = grids[b];
+  const int64_t n = (int64_t)min((unsigned long long)hit_cap, hit_count[b]);
+  const Hit* hb = hits + (int64_t)b * hit_cap;
+  const double Lx = (g.nx - 1) * g.dx, Ly = (g.ny - 1) * g.dy;
+  const double diag = sqrt(Lx * Lx + Ly * Ly);
+  double acc = 0.0;
+  for (int m = threadIdx.x; m < obs.n_obs; m += kChi2Threads) {
+    const int i = obs.sys[m];
+    const double ox = obs.x[m], oy = obs.y[m], sg = obs.sigma[m];
+    int64_t best = -1;
+    double bd = 0.0;
+    for (int64_t h = 0; h < n; ++h) {
+      if (hb[h].src != i) continue;
+      const double ex = ox - hb[h].x, ey = oy - hb[h].y;
+      const double d2 = ex * ex + ey * ey;
+      if (best < 0 || d2 < bd || (d2 == bd && hb[h].tri < hb[best].tri)) {
+        best = h;
+        bd = d2;
+      }
+    }
+    double term;
+    const int64_t o = (int64_t)sample * obs.n_obs + m;
+    if (best < 0) {
+      const double t = diag / sg;
+      term = t * t;
+      if (match_tri) match_tri[o] = -1;
+      if (match_hit) match_hit[o] = -1;
+      if (match_xy) { match_xy[2 * o] = 0.0; match_xy[2 * o + 1] = 0.0; }
+    } else {
+      term = bd / (sg * sg);
+      if (match_tri) match_tri[o] = hb[best].tri;
+      if (match_hit) match_hit[o] = (int32_t)best;
+      if (match_xy) { match_xy[2 * o] = hb[best].x; match_xy[2 * o + 1] = hb[best].y; }
+    }
+    acc = acc + term;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < kChi2Threads / 32; ++w) tot = tot + wsum[w];
+    chi2[sample] = tot;
+  }
+}
+
+cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, int n_samples,
+                        int64_t hit_cap, int sample_base, const SampleGrid* grids,
+                        const lt_obs& obs, double* chi2, int64_t* match_tri, int32_t* match_hit,
+                        double* match_xy, cudaStream_t st) {
+  if (n_samples <= 0) return cudaSuccess;
+  k_chi2<<<n_samples, kChi2Threads, 0, st>>>(hits, hit_count, hit_cap, sample_base, grids, obs,
+                                             chi2, match_tri, match_hit, match_xy);
+  return cudaGetLastError();
+}
+
+}  // namespace lt

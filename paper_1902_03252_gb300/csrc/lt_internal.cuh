@@ -1,0 +1,231 @@
+// Internal declarations of the GB300 chi^2 library: prepared potential
+// records, the FP64 and FP32 per-potential deflections, error-bound
+// constants, device status bits and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lt.h"
+
+namespace lt {
+
+// ------------------------------------------------------------------ status
+// Device-side status word (latched, OR-ed): reported by lt_model_sync.
+enum : uint32_t {
+  ST_OVERFLOW_HITS = 1u << 0,
+  ST_OVERFLOW_WORK = 1u << 1,
+  ST_NONFINITE = 1u << 2,
+};
+
+// Counters written by kernels (int64, device), one set per model.
+enum { CNT_HITS = 0, CNT_AMBIG, CNT_REFINE, CNT_FP64_NODES, CNT_DROPPED, CNT_N };
+
+constexpr double kC = 299792.458;         // km/s
+constexpr double kArcsec = 206264.80625;  // arcsec per radian
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kU32 = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
+
+// --------------------------------------------------------- prepared records
+// FP64 record of one potential, in parameter index order (16 doubles).  The
+// FP64 path sums potentials in index order with the formula order stated in
+// alpha64_one, so it reproduces an FP64 reference that follows the same
+// statement up to the ulps of the transcendental functions.
+struct Pot64 {
+  double kind, cx, cy, c, s, b0, e, q, k2, q2, a, sc, scale, pad0, pad1, pad2;
+};
+static_assert(sizeof(Pot64) == 128, "Pot64 layout");
+
+// FP32 record of one potential (5 float4 = 80 bytes), grouped by kind.
+//   SIS   : f[0] = {cx, cy, b0, 0}
+//   SIE   : f[0] = {cx, cy, c, s}; f[1] = {(1-eps), (1+eps), b0(1-eps), b0(1+eps)}
+//   PIEMD : f[0] = {cx, cy, c, s}; f[1] = {q2, q2*a*a, q2*s*s, k2};
+//           f[2] = {a, s, q2*a, q2*s}; f[3] = {s-a, q2(s+a)(s-a), q2(s-a), B}
+//   all   : f[4] = {errP0, errGx, errGy, errQ} (error-bound coefficients; SIS
+//           and SIE use errP0 only, errQ is summed into Seg32::q_tot)
+// errP0 * (4 Theta + |cx| + |cy|) is the translation-error coefficient of the
+// running bound (Theta = largest |node coordinate| of the grid).
+struct Pot32 {
+  float4 f[5];
+};
+static_assert(sizeof(Pot32) == 80, "Pot32 layout");
+
+// Per-sample kind segments of the FP32 records: [n_sis, n_piemd, n_sie, 0]
+// and the static part of the error bound, sum_k errQ_k (float).
+struct Seg32 {
+  int n_sis, n_piemd, n_sie;
+  float q_tot;
+};
+
+// ---------------------------------------------------- FP64 deflection (one)
+// atan(t)/t and atanh(t)/t as functions of t2 = t*t, with the short Taylor
+// branch for tiny arguments (keeps q -> 1 exact).
+__device__ __forceinline__ double atanc_sq64(double t2) {
+  if (t2 < 1e-6) return 1.0 - t2 * (1.0 / 3.0 - t2 * (1.0 / 5.0 - t2 * (1.0 / 7.0)));
+  double t = sqrt(t2);
+  return atan(t) / t;
+}
+__device__ __forceinline__ double atanhc_sq64(double t2) {
+  if (t2 < 1e-6) return 1.0 + t2 * (1.0 / 3.0 + t2 * (1.0 / 5.0 + t2 * (1.0 / 7.0)));
+  double t = sqrt(t2);
+  return atanh(t) / t;
+}
+
+// Scaled deflection of one potential at (x, y) in FP64.  Must be compiled
+// without FMA contraction (-fmad=false): every operation is rounded in the
+// order written.
+//   SIS  (Sect. 2.1): b0 (theta - c)/|theta - c|, zero at the centre.
+//   SIE  (Algorithm 1): translate, rotate by phi, R = sqrt(x'^2 (1-eps) +
+//        y'^2 (1+eps)), ((1-eps) b0 x'/R, (1+eps) b0 y'/R), rotate by -phi.
+//   PIEMD (dPIE core a, cut s, q = 1 - e): per cored term w in (a, s)
+//        psi = sqrt(q^2 (w^2 + x'^2) + y'^2), zx = x'/(psi + w),
+//        zy = y'/(psi + q^2 w), F = (zx atanc(k^2 zx^2), zy atanhc(k^2 zy^2));
+//        alpha' = b0 s/(s-a) [F(a) - F(s)], rotated by -phi.
+__device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, double& ax,
+                                            double& ay) {
+  double dx = x - p.cx;
+  double dy = y - p.cy;
+  int kind = (int)p.kind;
+  if (kind == LT_SIS) {
+    double R = sqrt(dx * dx + dy * dy);
+    if (R == 0.0) { ax = 0.0; ay = 0.0; return; }
+    ax = p.b0 * dx / R;
+    ay = p.b0 * dy / R;
+    return;
+  }
+  double xp = dx * p.c + dy * p.s;
+  double yp = dy * p.c - dx * p.s;
+  double gx, gy;
+  if (kind == LT_SIE) {
+    double R = sqrt(xp * xp * (1.0 - p.e) + yp * yp * (1.0 + p.e));
+    if (R == 0.0) { ax = 0.0; ay = 0.0; return; }
+    gx = (1.0 - p.e) * p.b0 * xp / R;
+    gy = (1.0 + p.e) * p.b0 * yp / R;
+  } else {
+    double fx0, fy0, fx1, fy1;
+    {
+      double w = p.a;
+      double psi = sqrt(p.q2 * (w * w + xp * xp) + yp * yp);
+      double zx = xp / (psi + w);
+      double zy = yp / (psi + p.q2 * w);
+      fx0 = zx * atanc_sq64(p.k2 * zx * zx);
+      fy0 = zy * atanhc_sq64(p.k2 * zy * zy);
+    }
+    {
+      double w = p.sc;
+      double psi = sqrt(p.q2 * (w * w + xp * xp) + yp * yp);
+      double zx = xp / (psi + w);
+      double zy = yp / (psi + p.q2 * w);
+      fx1 = zx * atanc_sq64(p.k2 * zx * zx);
+      fy1 = zy * atanhc_sq64(p.k2 * zy * zy);
+    }
+    gx = p.scale * (fx0 - fx1);
+    gy = p.scale * (fy0 - fy1);
+  }
+  ax = gx * p.c - gy * p.s;
+  ay = gy * p.c + gx * p.s;
+}
+
+// ---------------------------------------------------- FP32 special functions
+// atan(t)/t and atanh(t)/t of t2 = t*t >= 0 in FP32 (CUDA atanf / log1pf,
+// <= 2 ulp; Taylor branch below 1e-8).
+__device__ __forceinline__ float atanc_sq32(float t2) {
+  float t = sqrtf(t2);
+  float r = atanf(t) / t;
+  return t2 < 1e-8f ? 1.0f - t2 * (1.0f / 3.0f) : r;
+}
+__device__ __forceinline__ float atanhc_sq32(float t2) {
+  // atanh(t) = 0.5 log1p(2t / (1 - t))
+  float t = sqrtf(t2);
+  float r = 0.5f * log1pf(2.0f * t / (1.0f - t)) / t;
+  return t2 < 1e-8f ? 1.0f + t2 * (1.0f / 3.0f) : r;
+}
+
+// Launch-shape variants of the FP32 deflection kernel (autotuned).
+struct DeflectShape {
+  int threads;  // threads per block
+  int npt;      // nodes per thread
+};
+constexpr int kNumShapes = 4;
+__host__ __device__ inline DeflectShape deflect_shape(int v) {
+  const DeflectShape tab[kNumShapes] = {{256, 2}, {256, 4}, {128, 4}, {128, 8}};
+  return tab[v < 0 || v >= kNumShapes ? 1 : v];
+}
+
+// ----------------------------------------------------------- batch layout
+// One sample's grid and where its node / cell data live in a workspace.
+struct SampleGrid {
+  double x0, y0, dx, dy;
+  int nx, ny;
+  int64_t node_off;  // offset of node (0,0) in the node workspace
+  float theta_max;   // largest |coordinate| of any node
+  float pad;
+};
+
+// Work item of the FP64 stage: an ambiguous (triangle, source) pair or an
+// FP32 hit to re-interpolate.
+struct Work64 {
+  int32_t sample, src;
+  int64_t tri;
+  int32_t type;  // 0 = ambiguous pair, 1 = refine a certain hit
+  int32_t pad;
+};
+
+// Hit record kept between the search and the chi^2 kernels.
+struct Hit {
+  int32_t src, fp64;
+  int64_t tri;
+  double x, y;
+  double w[3];
+};
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return the cudaGetLastError() value.
+cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,
+                        Seg32* seg, uint32_t* status, cudaStream_t st);
+cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
+                             const SampleGrid* grids, const int64_t* item_off, int n_samples,
+                             int64_t n_items, int shape, float4* node_out, int sm_count,
+                             cudaStream_t st);
+cudaError_t launch_deflect64(const Pot64* pot64, int n_pot, const SampleGrid* grids,
+                             const int64_t* item_off, int n_samples, int64_t n_items,
+                             double2* node_out, int sm_count, cudaStream_t st);
+// Copy one sample's node workspace into a caller layout.
+cudaError_t launch_unpack32(const float4* nodes, int64_t n, float2* alpha, float* err,
+                            cudaStream_t st);
+
+// Sources of the triangle search: positions (FP64), ratios D_ls/D_s.
+struct Sources {
+  const double* xy;   // [batch][n_src][2]
+  const double* r;    // [batch][n_src] (stride_r = n_src) or [n_src] (stride_r = 0)
+  int n_src;
+  int stride_r;
+  int sample_base;    // sample index of the first sample in this chunk
+};
+
+cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const int64_t* item_off,
+                            int n_samples, int64_t n_items, Sources src, Hit* hits,
+                            int64_t hit_cap, Work64* work, int64_t work_cap,
+                            unsigned long long* hit_count, unsigned long long* work_count,
+                            long long* counters, uint32_t* status, int sm_count,
+                            cudaStream_t st);
+cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const int64_t* item_off,
+                            int n_samples, int64_t n_items, Sources src, Hit* hits,
+                            int64_t hit_cap, unsigned long long* hit_count, long long* counters,
+                            uint32_t* status, int sm_count, cudaStream_t st);
+cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* grids, Sources src,
+                             const Work64* work, const unsigned long long* work_count,
+                             int n_samples, int64_t work_cap, Hit* hits, int64_t hit_cap,
+                             unsigned long long* hit_count, long long* counters,
+                             uint32_t* status, int sm_count, cudaStream_t st);
+cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_count, int n_samples,
+                             int64_t hit_cap, int sample_base, lt_image* out, int64_t out_cap,
+                             int64_t* n_out, uint32_t* status, cudaStream_t st);
+cudaError_t launch_barycentres(const Pot64* pot64, int n_pot, int batch, const lt_obs& obs,
+                               double* beta_obs, double* bary, cudaStream_t st);
+cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, int n_samples,
+                        int64_t hit_cap, int sample_base, const SampleGrid* grids,
+                        const lt_obs& obs, double* chi2, int64_t* match_tri, int32_t* match_hit,
+                        double* match_xy, cudaStream_t st);
+
+}  // namespace lt

@@ -77,10 +77,26 @@ def make_c1():
     })
 
 
+def mapped_candidates(cfg_index: int, base_params, n: int, half_field: float):
+    """Candidate sources for a super-critical cluster: the source-plane
+    positions beta = theta - r alpha(theta) (oracle) of image-plane points
+    drawn uniformly over the field (half-width half_field / 2), so that every
+    candidate has at least one image.  Used where the summed convergence is
+    so high that the map is one-to-one except near the field edge, where the
+    critical curves lie."""
+    cand = W.source_candidates(cfg_index, n, half_field)
+    ax, ay, _ = oracle.alpha_points(base_params, cand[:, 0], cand[:, 1])
+    out = cand.copy()
+    out[:, 0] = cand[:, 0] - cand[:, 2] * ax
+    out[:, 1] = cand[:, 1] - cand[:, 2] * ay
+    return out
+
+
 def make_obs(cfg_name: str, cfg_index: int, base_params, grid: W.Grid, n_src: int,
-             half_field: float, n_candidates: int):
+             half_field: float, n_candidates: int, mapped: bool = False):
     t0 = time.time()
-    cand = W.source_candidates(cfg_index, n_candidates, half_field)
+    cand = (mapped_candidates(cfg_index, base_params, n_candidates, half_field) if mapped
+            else W.source_candidates(cfg_index, n_candidates, half_field))
     H, U = oracle.find_images(base_params, grid.as_tuple(), cand[:, :2], cand[:, 2],
                               n_threads=THREADS, capacity=1 << 20)
     by_src = {}
@@ -102,8 +118,10 @@ def make_obs(cfg_name: str, cfg_index: int, base_params, grid: W.Grid, n_src: in
         "config": cfg_name, "grid": list(grid.as_tuple()),
         "x": xy[:, 0].tolist(), "y": xy[:, 1].tolist(), "sigma": [SIGMA_OBS] * len(xs),
         "sys": sys_, "dls_ds": r, "src_true": cand[keep, :2].tolist(),
-        "how": "oracle images of multiply imaged candidate sources (central half of the "
-               "field) on the stated grid, plus N(0, 0.01\") noise per coordinate",
+        "how": ("oracle images of multiply imaged candidate sources (" +
+                ("lens-mapped image-plane points of the whole field"
+                 if mapped else "uniform in the central half of the field") +
+                ") on the stated grid, plus N(0, 0.01\") noise per coordinate"),
         "n_undecidable": len(U),
     })
     print(f"{cfg_name}: {len(keep)} systems, {len(xs)} images, {time.time() - t0:.1f}s")
@@ -123,7 +141,7 @@ def main(which):
         make_obs("c4", 4, w.params[0], w.obs_grid, w.n_src, 100.0, 300)
     if "c5" in which:
         w = W.c5(batch=1)
-        make_obs("c5", 5, w.notes["base"], w.obs_grid, w.n_src, 200.0, 800)
+        make_obs("c5", 5, w.notes["base"], w.obs_grid, w.n_src, 400.0, 1000, mapped=True)
 
 
 if __name__ == "__main__":

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (written in each test):
+* image sets: bit-exact (sample, source, triangle) sets, in FP64 and in mixed
+  precision, apart from pairs the oracle itself classifies as undecidable
+  between two FP64 evaluations (reported; expected to be none);
+* FP64 deflections: within 1e-12 of sum_k |alpha_k| (transcendental ulps);
+* FP32 deflections: within the node's own running error bound;
+* positions: 1e-9" (FP64 path) and 1e-4" (mixed; the stated FP32 position
+  bound is 2.5e-5");
+* chi^2: consistent with those position tolerances.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1902_03252_gb300 import lt, workloads as W  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lt.load(build_if_missing=True)
+
+
+def load_obs(cfg):
+    with open(os.path.join(GOLDEN, f"obs_{cfg}.json")) as f:
+        return json.load(f)
+
+
+def mixed_cluster(seed, n_pot=20, half=25.0):
+    """PIEMD + SIS + SIE mix for kind coverage."""
+    rng = np.random.default_rng(seed)
+    p = W.draw_piemd(rng, n_pot, half, 100.0, 900.0)
+    p[0, ::7] = W.SIS
+    p[0, 3::7] = W.SIE
+    p[3, 3::7] = rng.uniform(0, 0.3, p[3, 3::7].shape)
+    return p
+
+
+def to_set(imgs):
+    return {(int(r["src"]), int(r["tri"])) for r in imgs}
+
+
+def oracle_set(H):
+    return {(h["src"], h["tri"]) for h in H}
+
+
+def run_find(m, grids, src_xy, r, prec, cap=4096):
+    sx = torch.as_tensor(np.asarray(src_xy, dtype=np.float64), device="cuda")
+    rr = torch.as_tensor(np.asarray(r, dtype=np.float64), device="cuda")
+    out, n = m.find_images(grids, sx, rr, precision=prec, capacity=cap)
+    st, stats = m.sync()
+    return st, stats, lt.images_to_numpy(out, n), n.cpu().numpy()
+
+
+# ------------------------------------------------------------------ deflection
+@pytest.mark.parametrize("seed", [1, 2])
+def test_deflect_fp64_matches_oracle(oracle, seed):
+    p = mixed_cluster(seed)
+    grid = (-40.0, -37.0, 80.0 / 211, 74.0 / 187, 212, 188)
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    a = m.deflect_grid(grid, precision=lt.FP64).cpu().numpy()
+    ref, asum = oracle.deflect_grid(p, grid, n_threads=4)
+    err = np.abs(a - ref).max(axis=-1)
+    assert np.all(err <= 1e-12 * (asum + 1.0)), err.max()
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_deflect_mixed_within_running_bound(oracle, seed):
+    p = mixed_cluster(seed, n_pot=40)
+    grid = (-50.0, -50.0, 100.0 / 299, 100.0 / 299, 300, 300)
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+    a, e = a.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
+    ref, _ = oracle.deflect_grid(p, grid, n_threads=4)
+    d = np.abs(a - ref).max(axis=-1)
+    ratio = d / e
+    print(f"FP32 error / running bound: max {ratio.max():.3g}, median {np.median(ratio):.3g}")
+    assert np.all(np.isfinite(e)) and np.all(e > 0)
+    assert ratio.max() <= 1.0
+
+
+def test_deflect_c2_full_size_sampled(oracle):
+    """The 2000^2, 100-PIEMD grid in the benchmark's launch configuration:
+    every node within its bound on a sampled subset, FP64 on the same subset."""
+    w = W.c2()
+    grid = w.grids[0].as_tuple()
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+    a64 = m.deflect_grid(grid, precision=lt.FP64)
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, 2000 * 2000, 4000)
+    jj, ii = np.divmod(idx, 2000)
+    x = grid[0] + ii * grid[2]
+    y = grid[1] + jj * grid[3]
+    rx, ry, asum = oracle.alpha_points(w.params[0], x, y)
+    A = a.reshape(-1, 2).cpu().numpy()[idx].astype(np.float64)
+    E = e.reshape(-1).cpu().numpy()[idx].astype(np.float64)
+    A64 = a64.reshape(-1, 2).cpu().numpy()[idx]
+    d32 = np.maximum(np.abs(A[:, 0] - rx), np.abs(A[:, 1] - ry))
+    assert np.all(d32 <= E), (d32 / E).max()
+    d64 = np.maximum(np.abs(A64[:, 0] - rx), np.abs(A64[:, 1] - ry))
+    assert np.all(d64 <= 1e-12 * (asum + 1.0))
+
+
+# -------------------------------------------------------------- image search
+def check_images(oracle, p, grid, src, r, prec, pos_tol, exact_ties=False):
+    """exact_ties: the lens uses only correctly rounded operations (SIS), so
+    even pairs the oracle flags as ties must agree bit for bit."""
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    st, stats, imgs, n = run_find(m, [grid], np.asarray(src)[None], np.asarray(r)[None], prec)
+    assert st == lt.LT_OK
+    H, U = oracle.find_images(p, grid, src, r, n_threads=4)
+    und = {(u["src"], u["tri"]) for u in U}
+    got, exp = to_set(imgs[0]), oracle_set(H)
+    diff = got ^ exp
+    assert diff <= und, (sorted(diff - und)[:10], len(got), len(exp))
+    if exact_ties:
+        assert not diff, sorted(diff)[:10]
+    else:
+        assert not und, f"{len(und)} FP64-undecidable pairs"
+    ref = {(h["src"], h["tri"]): h for h in H}
+    worst = 0.0
+    for rec in imgs[0]:
+        h = ref[(int(rec["src"]), int(rec["tri"]))]
+        worst = max(worst, abs(rec["x"] - h["x"]), abs(rec["y"] - h["y"]))
+    assert worst <= pos_tol, worst
+    # sorted by (src, tri)
+    keys = [(int(r_["src"]), int(r_["tri"])) for r_ in imgs[0]]
+    assert keys == sorted(keys)
+    return stats, worst
+
+
+@pytest.mark.parametrize("prec,tol", [(lt.FP64, 1e-9), (lt.MIXED, 1e-4)])
+def test_find_images_sis(oracle, prec, tol):
+    w = W.c1()
+    g = w.grids[0].as_tuple()
+    # (0, 0) is the Einstein ring: on this grid, symmetric about the lens,
+    # mapped cell diagonals pass exactly through the source (tie rule)
+    src = [(2.0, 1.5), (0.0, 0.0), (-4.0, 6.0), (9.0, 8.0), (30.0, -2.0)]
+    check_images(oracle, w.params[0], g, src, [0.7] * len(src), prec, tol, exact_ties=True)
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+@pytest.mark.parametrize("prec,tol", [(lt.FP64, 1e-9), (lt.MIXED, 1e-4)])
+def test_find_images_cluster(oracle, seed, prec, tol):
+    p = mixed_cluster(seed, n_pot=30, half=20.0)
+    grid = (-30.0, -30.0, 60.0 / 333, 60.0 / 333, 334, 334)
+    rng = np.random.default_rng(seed)
+    src = rng.uniform(-8, 8, (12, 2))
+    r = rng.uniform(0.3, 0.9, 12)
+    stats, worst = check_images(oracle, p, grid, src, r, prec, tol)
+    print(f"prec {prec}: stats {stats}, worst position error {worst:.3g}")
+
+
+# ------------------------------------------------------------------- chi^2
+def check_chi2(oracle, w, o, prec, grids=None, graph=False):
+    grids = grids or [g.as_tuple() for g in w.grids]
+    obs = lt.Observations.from_dict(o)
+    m = lt.Model(w.n_pot, w.batch)
+    m.set_params(w.params)
+    c2 = m.chi2(grids, obs, precision=prec, graph=graph)
+    st, stats = m.sync()
+    assert st == lt.LT_OK, st
+    mt, mxy, bary = m.last_matches(len(o["x"]), len(o["dls_ds"]))
+    c2, mt, mxy, bary = c2.cpu().numpy(), mt.cpu().numpy(), mxy.cpu().numpy(), bary.cpu().numpy()
+    tol = 1e-4 if prec == lt.MIXED else 1e-9
+    for b in range(w.batch):
+        ref = oracle.chi2(w.params[b], grids[b], o, n_threads=4)
+        assert ref["n_undecidable"] == 0
+        np.testing.assert_allclose(bary[b], ref["bary"], rtol=0, atol=1e-11)
+        assert np.array_equal(mt[b], ref["match_tri"]), (b, mt[b], ref["match_tri"])
+        ok = ref["match_tri"] >= 0
+        assert np.all(np.abs(mxy[b][ok] - ref["match_xy"][ok]) <= tol)
+        res = np.hypot(np.asarray(o["x"]) - ref["match_xy"][:, 0],
+                       np.asarray(o["y"]) - ref["match_xy"][:, 1])
+        ctol = np.sum((2 * res * tol * 1.5 + 2 * tol * tol) / np.asarray(o["sigma"]) ** 2)
+        assert abs(c2[b] - ref["chi2"]) <= ctol + 1e-12 * ref["chi2"], (b, c2[b], ref["chi2"])
+    return c2, stats
+
+
+@pytest.mark.parametrize("prec", [lt.FP64, lt.MIXED])
+def test_chi2_c1(oracle, prec):
+    check_chi2(oracle, W.c1(), load_obs("c1"), prec)
+
+
+@pytest.mark.parametrize("prec", [lt.FP64, lt.MIXED])
+def test_chi2_c4(oracle, prec):
+    check_chi2(oracle, W.c4(), load_obs("c4"), prec)
+
+
+def test_chi2_batched_uneven(oracle):
+    """Eight perturbed samples on grids of uneven sizes in one call."""
+    w = W.c3(batch=8)
+    o = load_obs("c3")
+    rng = np.random.default_rng(3)
+    grids = [W.Grid.square(200.0, int(n)).as_tuple() for n in rng.integers(300, 700, 8)]
+    check_chi2(oracle, w, o, lt.MIXED, grids=grids)
+
+
+def test_graph_replay_matches_direct(oracle):
+    w = W.c4()
+    o = load_obs("c4")
+    obs = lt.Observations.from_dict(o)
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    g = [w.grids[0].as_tuple()]
+    direct = m.chi2(g, obs, precision=lt.MIXED).clone()
+    outs = [m.chi2(g, obs, precision=lt.MIXED, graph=True).clone() for _ in range(3)]
+    assert m.sync()[0] == lt.LT_OK
+    for o_ in outs:
+        assert torch.equal(o_, direct)
+
+
+# -------------------------------------------------------------- edge cases
+def test_edge_cases(oracle):
+    w = W.c1()
+    m = lt.Model(1, 1)
+    m.set_params(w.params)
+    # a 1 x 1 grid and a 1-row grid have no triangles
+    for g in [(0.0, 0.0, 1.0, 1.0, 1, 1), (0.0, 0.0, 1.0, 1.0, 7, 1)]:
+        st, stats, imgs, n = run_find(m, [g], [[(0.5, 0.5)]], [[0.7]], lt.MIXED)
+        assert st == lt.LT_OK and n[0] == 0
+    # no sources
+    out, n = m.find_images([w.grids[0]], None, None, precision=lt.MIXED, capacity=16)
+    assert m.sync()[0] == lt.LT_OK and int(n.cpu()[0]) == 0
+    # capacity overflow is reported, and the true count returned
+    st, stats, imgs, n = run_find(m, [w.grids[0]], [[(0.0, 0.0)]], [[0.7]], lt.MIXED, cap=8)
+    assert st == lt.LT_ERR_OVERFLOW and n[0] > 8 and len(imgs[0]) == 8
+    # invalid parameters are latched
+    bad = w.params.copy()
+    bad[0, 7, 0] = np.nan
+    m.set_params(bad)
+    assert m.sync()[0] == lt.LT_ERR_NONFINITE
+    bad = W.c2().params[:, :, :3].copy()
+    bad[0, 5, 1] = -1.0  # negative core radius
+    m3 = lt.Model(3, 1)
+    m3.set_params(bad)
+    assert m3.sync()[0] == lt.LT_ERR_NONFINITE
+    # argument errors
+    with pytest.raises(lt.LTError):
+        m.deflect_grid((0.0, 0.0, -1.0, 1.0, 4, 4))
+    with pytest.raises(lt.LTError):
+        m.deflect_grid((0.0, 0.0, 1.0, 1.0, 4, 4), sample=3)
