@@ -127,12 +127,23 @@ def measured_peaks():
         return {}
 
 
-def traffic_for(kernel: str, source: str):
+def source_sha(files) -> str:
+    """sha256 over the concatenated kernel sources (csrc/ file names)."""
+    h = hashlib.sha256()
+    for name in files:
+        with open(os.path.join(ROOT, "paper_1902_03252_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# the kernel sources and the build flags (-ftz etc.) they are compiled with
+DEFLECT32_SOURCES = ("lt_fp32.cu", "lt_fp32.cuh", "lt_internal.cuh", "../_build.py")
+
+
+def traffic_for(kernel: str, files):
     """DRAM traffic per launch recorded in profiles/<kernel>_*.md, if the kernel
-    source has not changed since the capture (else None)."""
-    src_path = os.path.join(ROOT, "paper_1902_03252_gb300", "csrc", source)
-    with open(src_path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
+    sources have not changed since the capture (else None)."""
+    sha = source_sha(files)
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
@@ -141,10 +152,11 @@ def traffic_for(kernel: str, source: str):
             continue
         with open(os.path.join(pdir, name)) as f:
             txt = f.read()
-        m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-        m2 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-        if m1 and m2 and m2.group(1) == sha:
-            return float(m1.group(1))
+        for section in txt.split("\n### "):
+            m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", section)
+            m2 = re.search(r"source_sha256:\s*([0-9a-f]{64})", section)
+            if m1 and m2 and m2.group(1) == sha:
+                return float(m1.group(1))
     return None
 
 
@@ -319,7 +331,7 @@ def run_ours(a, rank, world, local):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak = sm_count * f_max * PIEMD_NODE_POT_PER_SM_CLK / 1e9
-    traffic = traffic_for("k_deflect32", "lt_fp32.cu")
+    traffic = traffic_for("k_deflect32", DEFLECT32_SOURCES)
     d64 = prof64["deflect"]
     defl64_ms = d64["ms"] / max(1, d64["launches"])
     launches_per_step = sum(prof[k]["launches"] for k in prof) / a.steps
@@ -353,6 +365,7 @@ def run_ours(a, rank, world, local):
         "clocks": clk,
         "gpu_launches": int(round(launches_per_step * a.steps)),
         "wall_s_timed_region": wall,
+        "deflect32_source_sha256": source_sha(DEFLECT32_SOURCES),
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(w, o)

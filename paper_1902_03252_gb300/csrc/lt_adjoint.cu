@@ -1,0 +1,319 @@
+// Hand-written adjoint of the chi^2 path with the triangle assignment and the
+// image matching of the forward evaluation held fixed.
+//
+// chi^2 = sum_m |x_obs,m - x_m|^2 / sigma_m^2 (Eq. 8) with
+//   x_m = theta_A + w_B (theta_B - theta_A) + w_C (theta_C - theta_A) inside the
+//   matched triangle, where (w_B, w_C) solve
+//   [beta_B - beta_A, beta_C - beta_A] (w_B, w_C)^T = beta_bar - beta_A,
+//   beta_v = theta_v - r alpha(theta_v) (Eq. 11) and beta_bar the system's
+//   barycentre of theta_obs - r alpha(theta_obs).
+// With G = dchi^2/dx of a predicted image and lambda = M^-T (G.(theta_B -
+// theta_A), G.(theta_C - theta_A)), dchi^2 = lambda . (dbeta_bar - sum_v w_v
+// dbeta_v), so every parameter derivative is a sum over "adjoint points"
+// (the three vertices of each matched triangle, coefficient r w_v lambda, and
+// every observed image of the system, coefficient -(r/n) sum lambda) of
+// coefficient . d alpha_k(point) / d p_k.
+//
+//   k_adj_hits / k_adj_bary  build those points and coefficients (vertex
+//                deflections of matched triangles recomputed in FP64);
+//   k_adj_grad   one thread per potential: the 2x6 Jacobian of its deflection
+//                w.r.t. (x, y, e, phi, r_core, sigma_v) at every point, in
+//                FP32, contracted with the coefficients; FP32 partial sums of
+//                32 points are accumulated in FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lt_internal.cuh"
+
+namespace lt {
+
+constexpr int kAdjThreads = 128;
+constexpr int kAdjChunk = 256;
+
+// ------------------------------------------------------------ coefficients
+// Pass 1, one warp per (sample, observed image m): if m is the first observed
+// image matched to its predicted image h, build h's three vertex points.  The
+// vertex deflections are recomputed in FP64 (lanes split the potentials,
+// sums in index order): M = [beta_B - beta_A, beta_C - beta_A] is a
+// difference of large deflections and its FP32 rounding would be amplified
+// by M's conditioning in magnified triangles.
+constexpr int kAdjWarps = 4;
+
+__global__ void __launch_bounds__(32 * kAdjWarps)
+    k_adj_hits(const Pot64* __restrict__ pot64, int n_pot, int batch,
+               const SampleGrid* __restrict__ grids, const Hit* __restrict__ hits,
+               int64_t hit_cap, lt_obs obs, const int32_t* __restrict__ match_hit,
+               double2* __restrict__ lam, AdjPt* __restrict__ pts, int P) {
+  __shared__ double2 buf[kAdjWarps][3 * 32];
+  __shared__ double res[kAdjWarps][6];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * kAdjWarps;
+  for (int64_t f = (int64_t)blockIdx.x * kAdjWarps + wid; f < (int64_t)batch * obs.n_obs;
+       f += nw) {
+    const int b = (int)(f / obs.n_obs);
+    const int m = (int)(f - (int64_t)b * obs.n_obs);
+    const int32_t* mh = match_hit + (int64_t)b * obs.n_obs;
+    AdjPt* pp = pts + (int64_t)b * P;
+    const int h = mh[m];
+    bool owner = h >= 0;
+    for (int k = 0; k < m && owner; ++k) owner = mh[k] != h;
+    if (!owner) {  // warp-uniform
+      if (lane < 3) pp[3 * m + lane] = AdjPt{0.0, 0.0, 0.0, 0.0};
+      if (lane == 0) lam[f] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const SampleGrid g = grids[b];
+    const Hit H = hits[(int64_t)b * hit_cap + h];
+    // triangle vertices: T0 = (00, 10, 11), T1 = (00, 11, 01)
+    const int64_t cell = H.tri / 2;
+    const int t = (int)(H.tri % 2);
+    const int i = (int)(cell % (g.nx - 1)), j = (int)(cell / (g.nx - 1));
+    const int di[3] = {0, 1, t == 0 ? 1 : 0};
+    const int dj[3] = {0, t == 0 ? 0 : 1, 1};
+    double TX[3], TY[3];
+    for (int v = 0; v < 3; ++v) {
+      TX[v] = g.x0 + (double)(i + di[v]) * g.dx;
+      TY[v] = g.y0 + (double)(j + dj[v]) * g.dy;
+    }
+    warp_alpha64(pot64 + (int64_t)b * n_pot, n_pot, 3, TX, TY, &res[wid][0], &res[wid][3],
+                 buf[wid]);
+    if (lane == 0) {
+      // dchi^2/dx of this predicted image, over every observed image matched to it
+      double Gx = 0.0, Gy = 0.0;
+      for (int k = m; k < obs.n_obs; ++k) {
+        if (mh[k] != h) continue;
+        const double s2 = obs.sigma[k] * obs.sigma[k];
+        Gx += -2.0 * (obs.x[k] - H.x) / s2;
+        Gy += -2.0 * (obs.y[k] - H.y) / s2;
+      }
+      const double r = obs.dls_ds[obs.sys[m]];
+      double BX[3], BY[3];
+      for (int v = 0; v < 3; ++v) {
+        BX[v] = TX[v] - r * res[wid][v];
+        BY[v] = TY[v] - r * res[wid][3 + v];
+      }
+      const double M00 = BX[1] - BX[0], M01 = BX[2] - BX[0];
+      const double M10 = BY[1] - BY[0], M11 = BY[2] - BY[0];
+      const double det = M00 * M11 - M01 * M10;
+      const double dB = Gx * (TX[1] - TX[0]) + Gy * (TY[1] - TY[0]);
+      const double dC = Gx * (TX[2] - TX[0]) + Gy * (TY[2] - TY[0]);
+      // lambda = M^-T (dB, dC)
+      const double lx = (M11 * dB - M10 * dC) / det;
+      const double ly = (-M01 * dB + M00 * dC) / det;
+      lam[f] = make_double2(lx, ly);
+      for (int v = 0; v < 3; ++v)
+        pp[3 * m + v] = AdjPt{TX[v], TY[v], r * H.w[v] * lx, r * H.w[v] * ly};
+    }
+    __syncwarp();
+  }
+}
+
+// Pass 2: every observed image of system i is a barycentre point with
+// coefficient -(r_i / n_i) sum over the system's predicted images of lambda.
+__global__ void k_adj_bary(int batch, lt_obs obs, const double2* __restrict__ lam,
+                           AdjPt* __restrict__ pts, int P) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)batch * obs.n_obs) return;
+  const int b = (int)(f / obs.n_obs);
+  const int m = (int)(f - (int64_t)b * obs.n_obs);
+  const int i = obs.sys[m];
+  const double2* lb = lam + (int64_t)b * obs.n_obs;
+  double Lx = 0.0, Ly = 0.0;
+  int n = 0;
+  for (int k = 0; k < obs.n_obs; ++k) {
+    if (obs.sys[k] != i) continue;
+    ++n;
+    Lx += lb[k].x;
+    Ly += lb[k].y;
+  }
+  const double fct = -obs.dls_ds[i] / n;
+  pts[(int64_t)b * P + 3 * obs.n_obs + m] = AdjPt{obs.x[m], obs.y[m], fct * Lx, fct * Ly};
+}
+
+// --------------------------------------------------------------- Jacobians
+// atan(sqrt t)/sqrt t, atanh(sqrt t)/sqrt t and their t-derivatives.
+__device__ __forceinline__ void atanc_d(float t, float& A, float& dA) {
+  if (t < 0.05f) {
+    A = 1.f - t * (1.f / 3 - t * (1.f / 5 - t * (1.f / 7 - t * (1.f / 9))));
+    dA = -1.f / 3 + t * (2.f / 5 - t * (3.f / 7 - t * (4.f / 9 - t * (5.f / 11))));
+  } else {
+    const float s = sqrtf(t);
+    A = atanf(s) / s;
+    dA = (1.f / (1.f + t) - A) / (2.f * t);
+  }
+}
+__device__ __forceinline__ void atanhc_d(float t, float& H, float& dH) {
+  if (t < 0.05f) {
+    H = 1.f + t * (1.f / 3 + t * (1.f / 5 + t * (1.f / 7 + t * (1.f / 9))));
+    dH = 1.f / 3 + t * (2.f / 5 + t * (3.f / 7 + t * (4.f / 9 + t * (5.f / 11))));
+  } else {
+    const float s = sqrtf(t);
+    H = 0.5f * log1pf(2.f * s / (1.f - s)) / s;
+    dH = (1.f / (1.f - t) - H) / (2.f * t);
+  }
+}
+
+// One cored isothermal term F(w) = (atan(k zx)/k, atanh(k zy)/k) of the
+// PIEMD in its own frame and its derivatives w.r.t. x', y', q and w.
+struct CoredD {
+  float Fx, Fy, Fx_x, Fx_y, Fy_x, Fy_y, Fx_q, Fy_q, Fx_w, Fy_w;
+};
+__device__ __forceinline__ CoredD cored_d(float xp, float yp, float q, float w) {
+  const float q2 = q * q, T = (1.f - q) * (1.f + q);
+  const float psi = sqrtf(q2 * (w * w + xp * xp) + yp * yp);
+  const float Dx = psi + w, Dy = psi + q2 * w;
+  const float zx = xp / Dx, zy = yp / Dy;
+  float A, dA, H, dH;
+  atanc_d(T * zx * zx, A, dA);
+  atanhc_d(T * zy * zy, H, dH);
+  const float fzx = 1.f / (1.f + T * zx * zx), fzy = 1.f / (1.f - T * zy * zy);
+  const float ipsi = 1.f / psi;
+  const float px = q2 * xp * ipsi, py = yp * ipsi, pq = q * (w * w + xp * xp) * ipsi,
+              pw = q2 * w * ipsi;
+  const float zx_x = (1.f - zx * px) / Dx, zx_y = -zx * py / Dx, zx_q = -zx * pq / Dx,
+              zx_w = -zx * (pw + 1.f) / Dx;
+  const float zy_x = -zy * px / Dy, zy_y = (1.f - zy * py) / Dy,
+              zy_q = -zy * (pq + 2.f * q * w) / Dy, zy_w = -zy * (pw + q2) / Dy;
+  CoredD d;
+  d.Fx = zx * A;
+  d.Fy = zy * H;
+  d.Fx_x = fzx * zx_x;
+  d.Fx_y = fzx * zx_y;
+  d.Fy_x = fzy * zy_x;
+  d.Fy_y = fzy * zy_y;
+  d.Fx_q = fzx * zx_q - 2.f * q * zx * zx * zx * dA;
+  d.Fy_q = fzy * zy_q - 2.f * q * zy * zy * zy * dH;
+  d.Fx_w = fzx * zx_w;
+  d.Fy_w = fzy * zy_w;
+  return d;
+}
+
+// Contract c . d alpha / d (x_c, y_c, e, phi, r_core, sigma_v) for one
+// potential at (x, y) (FP32).  P: FP64 record (index order).
+__device__ __forceinline__ void contract(const Pot64& P, float x, float y, float cx, float cy,
+                                         float out[6]) {
+  const int kind = (int)P.kind;
+  const float dx = x - (float)P.cx, dy = y - (float)P.cy;
+  const float b0 = (float)P.b0;
+  for (int k = 0; k < 6; ++k) out[k] = 0.f;
+  if (kind == LT_SIS) {
+    const float R2 = dx * dx + dy * dy;
+    if (!(R2 > 0.f)) return;
+    const float iR = rsqrtf(R2), ux = dx * iR, uy = dy * iR;
+    const float s = b0 * iR;  // d alpha / d theta = s (I - u u^T)
+    const float cu = cx * ux + cy * uy;
+    // d alpha / d c = -(d alpha / d theta)
+    out[0] = -s * (cx - cu * ux);
+    out[1] = -s * (cy - cu * uy);
+    const float sv = (float)P.sv;
+    if (sv > 0.f) out[5] = 2.f / sv * b0 * cu;
+    return;
+  }
+  const float c = (float)P.c, sn = (float)P.s;
+  const float xp = dx * c + dy * sn, yp = dy * c - dx * sn;
+  // coefficient in the lens frame: c' = R(phi) c
+  const float cpx = c * cx + sn * cy, cpy = -sn * cx + c * cy;
+  float gx, gy, J00, J01, J10, J11, ge_x, ge_y, ga_x = 0.f, ga_y = 0.f;
+  if (kind == LT_SIE) {
+    const float e = (float)P.e;
+    const float R2 = (1.f - e) * xp * xp + (1.f + e) * yp * yp;
+    if (!(R2 > 0.f)) return;
+    const float iR = rsqrtf(R2), iR3 = iR * iR * iR;
+    const float ax = b0 * (1.f - e), ay = b0 * (1.f + e);
+    gx = ax * xp * iR;
+    gy = ay * yp * iR;
+    J00 = ax * (iR - (1.f - e) * xp * xp * iR3);
+    J01 = -ax * (1.f + e) * xp * yp * iR3;
+    J10 = -ay * (1.f - e) * xp * yp * iR3;
+    J11 = ay * (iR - (1.f + e) * yp * yp * iR3);
+    const float dR = 0.5f * (yp * yp - xp * xp) * iR;  // dR/deps
+    ge_x = b0 * (-xp * iR - (1.f - e) * xp * dR * iR * iR);
+    ge_y = b0 * (yp * iR - (1.f + e) * yp * dR * iR * iR);
+  } else {
+    const float q = (float)P.q, a = (float)P.a, s = (float)P.sc;
+    const float Bu = s / (s - a);  // unit-b0 scale
+    const CoredD A = cored_d(xp, yp, q, a), S = cored_d(xp, yp, q, s);
+    const float B = b0 * Bu;
+    gx = B * (A.Fx - S.Fx);
+    gy = B * (A.Fy - S.Fy);
+    J00 = B * (A.Fx_x - S.Fx_x);
+    J01 = B * (A.Fx_y - S.Fx_y);
+    J10 = B * (A.Fy_x - S.Fy_x);
+    J11 = B * (A.Fy_y - S.Fy_y);
+    // parameter e: q = 1 - e
+    ge_x = -B * (A.Fx_q - S.Fx_q);
+    ge_y = -B * (A.Fy_q - S.Fy_q);
+    const float dBu = s / ((s - a) * (s - a));
+    ga_x = b0 * (dBu * (A.Fx - S.Fx) + Bu * A.Fx_w);
+    ga_y = b0 * (dBu * (A.Fy - S.Fy) + Bu * A.Fy_w);
+  }
+  // d alpha / d theta = R(-phi) J R(phi); c . that = (c'^T J) R(phi)
+  const float r0 = cpx * J00 + cpy * J10, r1 = cpx * J01 + cpy * J11;
+  out[0] = -(r0 * c - r1 * sn);
+  out[1] = -(r0 * sn + r1 * c);
+  out[2] = cpx * ge_x + cpy * ge_y;
+  // d alpha / d phi = R(-phi) [(-gy, gx) + J (y', -x')]
+  out[3] = cpx * (-gy + J00 * yp - J01 * xp) + cpy * (gx + J10 * yp - J11 * xp);
+  out[4] = cpx * ga_x + cpy * ga_y;
+  // alpha is proportional to sigma_v^2
+  const float sv = (float)P.sv;
+  if (sv > 0.f) out[5] = 2.f / sv * (cpx * gx + cpy * gy);
+}
+
+__global__ void __launch_bounds__(kAdjThreads)
+    k_adj_grad(const Pot64* __restrict__ pot64, int n_pot, const AdjPt* __restrict__ pts, int P,
+               double* __restrict__ grad) {
+  __shared__ AdjPt sp[kAdjChunk];
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * kAdjThreads + threadIdx.x;
+  const bool valid = k < n_pot;
+  const Pot64 p = pot64[(int64_t)b * n_pot + (valid ? k : 0)];
+  const AdjPt* pb = pts + (int64_t)b * P;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int c0 = 0; c0 < P; c0 += kAdjChunk) {
+    const int cn = min(kAdjChunk, P - c0);
+    __syncthreads();
+    for (int v = threadIdx.x; v < cn; v += kAdjThreads) sp[v] = pb[c0 + v];
+    __syncthreads();
+    float part[6] = {0, 0, 0, 0, 0, 0};
+    for (int v = 0; v < cn; ++v) {
+      const AdjPt q = sp[v];
+      if (q.cx == 0.0 && q.cy == 0.0) continue;
+      float o[6];
+      contract(p, (float)q.x, (float)q.y, (float)q.cx, (float)q.cy, o);
+      for (int m = 0; m < 6; ++m) part[m] += o[m];
+      if ((v & 31) == 31) {
+        for (int m = 0; m < 6; ++m) {
+          acc[m] += part[m];
+          part[m] = 0.f;
+        }
+      }
+    }
+    for (int m = 0; m < 6; ++m) acc[m] += part[m];
+  }
+  if (valid)
+    for (int m = 0; m < 6; ++m) grad[((int64_t)b * n_pot + k) * 6 + m] = acc[m];
+}
+
+cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const SampleGrid* grids,
+                           const Hit* hits, int64_t hit_cap, const lt_obs& obs,
+                           const int32_t* match_hit, double2* lam, AdjPt* pts, double* grad,
+                           int sm_count, cudaStream_t st) {
+  const int P = 4 * obs.n_obs;
+  const int64_t warps = (int64_t)batch * obs.n_obs;
+  int64_t blocks = (warps + kAdjWarps - 1) / kAdjWarps;
+  if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
+  k_adj_hits<<<(unsigned)blocks, 32 * kAdjWarps, 0, st>>>(pot64, n_pot, batch, grids, hits,
+                                                          hit_cap, obs, match_hit, lam, pts, P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_adj_bary<<<(unsigned)((warps + 127) / 128), 128, 0, st>>>(batch, obs, lam, pts, P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid((n_pot + kAdjThreads - 1) / kAdjThreads, batch);
+  k_adj_grad<<<grid, kAdjThreads, 0, st>>>(pot64, n_pot, pts, P, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace lt

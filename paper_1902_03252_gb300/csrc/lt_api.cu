@@ -73,6 +73,8 @@ struct lt_model {
   int64_t* d_match_tri = nullptr;
   int32_t* d_match_hit = nullptr;
   double* d_match_xy = nullptr;
+  double2* d_adj_lam = nullptr;   // adjoint: lambda per matched observed image
+  AdjPt* d_adj_pts = nullptr;   // adjoint points (x, y, coefficient) [batch][4 n_obs]
   int obs_alloc = 0, sys_alloc = 0;
   int last_nobs = -1, last_nsys = -1;
   // CUDA graph cache of lt_chi2_graph
@@ -287,12 +289,16 @@ lt_status ensure_obs(lt_model* m, int n_obs, int n_sys) {
     if (m->d_match_tri) LT_CUDA(cudaFree(m->d_match_tri));
     if (m->d_match_hit) LT_CUDA(cudaFree(m->d_match_hit));
     if (m->d_match_xy) LT_CUDA(cudaFree(m->d_match_xy));
+    if (m->d_adj_lam) LT_CUDA(cudaFree(m->d_adj_lam));
+    if (m->d_adj_pts) LT_CUDA(cudaFree(m->d_adj_pts));
     m->d_beta_obs = nullptr; m->d_match_tri = nullptr; m->d_match_hit = nullptr;
-    m->d_match_xy = nullptr;
+    m->d_match_xy = nullptr; m->d_adj_lam = nullptr; m->d_adj_pts = nullptr;
     LT_CUDA(cudaMalloc(&m->d_beta_obs, sizeof(double) * 2 * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_match_tri, sizeof(int64_t) * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_match_hit, sizeof(int32_t) * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_match_xy, sizeof(double) * 2 * (size_t)m->batch * n_obs));
+    LT_CUDA(cudaMalloc(&m->d_adj_lam, sizeof(double2) * (size_t)m->batch * n_obs));
+    LT_CUDA(cudaMalloc(&m->d_adj_pts, sizeof(AdjPt) * 4 * (size_t)m->batch * n_obs));
     m->obs_alloc = n_obs;
   }
   if (n_sys > m->sys_alloc) {
@@ -483,7 +489,7 @@ void lt_model_destroy(lt_model* m) {
   void* ptrs[] = {m->d_params, m->d_pot64, m->d_pot32, m->d_seg, m->d_status, m->d_counters,
                   m->d_nodes, m->d_hits, m->d_work, m->d_hit_count, m->d_work_count,
                   m->d_plan_grids, m->d_plan_items, m->d_beta_obs, m->d_bary, m->d_match_tri,
-                  m->d_match_hit, m->d_match_xy};
+                  m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -665,9 +671,14 @@ lt_status lt_chi2_grad(lt_model* m, const lt_grid* grids, const lt_obs* obs,
                        lt_precision precision, double* chi2_out, double* grad_out,
                        uintptr_t stream) {
   if (!m) return LT_ERR_INVALID_ARG;
-  (void)grids; (void)obs; (void)precision; (void)chi2_out; (void)grad_out; (void)stream;
-  m->err = "lt_chi2_grad: not built yet";
-  return LT_ERR_INVALID_ARG;
+  LT_CHECK_ARG(grad_out != nullptr, "grad_out is NULL");
+  lt_status s = lt_chi2(m, grids, obs, precision, chi2_out, stream);
+  if (s != LT_OK) return s;
+  cudaStream_t st = S(stream);
+  LT_CUDA(launch_adjoint(m->d_pot64, m->n_pot, m->batch, m->d_plan_grids, m->d_hits,
+                         m->hits_cap_alloc, *obs, m->d_match_hit, m->d_adj_lam, m->d_adj_pts,
+                         grad_out, m->sm_count, st));
+  return LT_OK;
 }
 
 lt_status lt_last_matches(lt_model* m, int64_t* match_tri, double* match_xy, double* bary,

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "lt_internal.cuh"
+#include "lt_fp32.cuh"
 
 namespace lt {
 
@@ -26,76 +27,6 @@ __device__ __forceinline__ int find_sample(const int64_t* off, int n, int64_t it
 }
 
 // --------------------------------------------------------------- deflection
-// One SIS: alpha += b0 (theta - c)/R (zero at the centre).  err accumulates in
-// units of the FP32 unit roundoff.
-__device__ __forceinline__ void sis32(const float4* f, float P, float x, float y, float& ax,
-                                      float& ay, float& err) {
-  float dx = x - f[0].x, dy = y - f[0].y;
-  float R2 = fmaf(dx, dx, dy * dy);
-  float ri = R2 > 0.0f ? rsqrtf(R2) : 0.0f;
-  float g = f[0].z * ri;
-  ax = fmaf(g, dx, ax);
-  ay = fmaf(g, dy, ay);
-  err = fmaf(P, ri, err);
-  err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
-}
-
-// One SIE (Algorithm 1).
-__device__ __forceinline__ void sie32(const float4* f, float P, float x, float y, float& ax,
-                                      float& ay, float& err) {
-  float dx = x - f[0].x, dy = y - f[0].y;
-  float c = f[0].z, s = f[0].w;
-  float xp = fmaf(dx, c, dy * s);
-  float yp = fmaf(dy, c, -(dx * s));
-  float R2 = fmaf(xp * xp, f[1].x, yp * yp * f[1].y);
-  float ri = R2 > 0.0f ? rsqrtf(R2) : 0.0f;
-  float gx = f[1].z * xp * ri;
-  float gy = f[1].w * yp * ri;
-  ax = fmaf(gx, c, fmaf(-gy, s, ax));
-  ay = fmaf(gy, c, fmaf(gx, s, ay));
-  err = fmaf(P, ri, err);
-  err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
-}
-
-// One PIEMD (dPIE) in difference form.  With psi_w = sqrt(q^2(w^2+x'^2)+y'^2),
-// F(a) - F(s) is evaluated as one atan / atanh of
-//   tx = x' ds_x / ((psi_a+a)(psi_s+s) + k^2 x'^2),
-//   ty = y' ds_y / ((psi_a+q^2 a)(psi_s+q^2 s) - k^2 y'^2),
-// ds_x = (s-a)(1 + q^2 (s+a)/(psi_a+psi_s)), ds_y = q^2 (s-a)(1 + (s+a)/(psi_a+psi_s))
-// (atan u - atan v = atan((u-v)/(1+uv)), atanh likewise, and
-// psi_s - psi_a = q^2 (s^2-a^2)/(psi_a+psi_s)), which avoids the cancellation
-// of the two cored terms and halves the transcendental work.
-__device__ __forceinline__ void piemd32(const float4* f, float P, float x, float y, float& ax,
-                                        float& ay, float& err) {
-  float dx = x - f[0].x, dy = y - f[0].y;
-  float c = f[0].z, s = f[0].w;
-  float xp = fmaf(dx, c, dy * s);
-  float yp = fmaf(dy, c, -(dx * s));
-  float x2 = xp * xp, y2 = yp * yp;
-  float t = fmaf(f[1].x, x2, y2);
-  float pa2 = t + f[1].y, ps2 = t + f[1].z;
-  float ra = rsqrtf(pa2), rs = rsqrtf(ps2);
-  float pa = pa2 * ra, ps = ps2 * rs;
-  float iD = __fdividef(1.0f, pa + ps);
-  float dsx = fmaf(f[3].y, iD, f[3].x);
-  float dsy = fmaf(f[3].y, iD, f[3].z);
-  float px = (pa + f[2].x) * (ps + f[2].y);
-  float py = (pa + f[2].z) * (ps + f[2].w);
-  float k2 = f[1].w;
-  float denx = fmaf(k2, x2, px);
-  float deny = fmaf(-k2, y2, py);
-  float tx = __fdividef(xp * dsx, denx);
-  float ty = __fdividef(yp * dsy, deny);
-  float B = f[3].w;
-  float gx = B * tx * atanc_sq32(k2 * tx * tx);
-  float gy = B * ty * atanhc_sq32(k2 * ty * ty);
-  ax = fmaf(gx, c, fmaf(-gy, s, ax));
-  ay = fmaf(gy, c, fmaf(gx, s, ay));
-  err = fmaf(P, ra, err);
-  err = fmaf(f[4].y, fabsf(gx), fmaf(f[4].z, fabsf(gy), err));
-  err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
-}
-
 template <int NT, int NPT>
 __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot32,
                                                   const Seg32* __restrict__ seg, int n_pot,
@@ -300,6 +231,15 @@ __device__ __forceinline__ void warp_append_work(bool flag, const Work64& wk, Wo
   }
 }
 
+__device__ __forceinline__ float warp_min(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __global__ void __launch_bounds__(kSearchThreads)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
@@ -330,6 +270,18 @@ __global__ void __launch_bounds__(kSearchThreads)
     const float l00 = fabsf(v00.x) + fabsf(v00.y), l10 = fabsf(v10.x) + fabsf(v10.y);
     const float l01 = fabsf(v01.x) + fabsf(v01.y), l11 = fabsf(v11.x) + fabsf(v11.y);
     const float lmax = fmaxf(fmaxf(l00, l10), fmaxf(l01, l11));
+    // Conservative source-plane box of the warp's 32 cells for any r > 0:
+    // beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x].
+    const float inf = __int_as_float(0x7f800000);
+    const float W_tx0 = warp_min(valid ? xl : inf), W_tx1 = warp_max(valid ? xr : -inf);
+    const float W_ty0 = warp_min(valid ? yb : inf), W_ty1 = warp_max(valid ? yt : -inf);
+    const float W_ax0 = warp_min(valid ? fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)) : inf);
+    const float W_ax1 = warp_max(valid ? fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)) : -inf);
+    const float W_ay0 = warp_min(valid ? fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)) : inf);
+    const float W_ay1 = warp_max(valid ? fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)) : -inf);
+    const float W_e = warp_max(valid ? emax : 0.0f);
+    const float W_l = warp_max(valid ? lmax : 0.0f);
+    const bool W_any = __any_sync(0xffffffffu, valid);
     const double* sxy = src.xy + (int64_t)sample * src.n_src * 2;
     const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
     for (int s0 = 0; s0 < src.n_src; s0 += kMaxSrcSmem) {
@@ -343,6 +295,19 @@ __global__ void __launch_bounds__(kSearchThreads)
       __syncthreads();
       for (int k = 0; k < sn; ++k) {
         const SrcSmem S = ss[k];
+        {
+          // warp-uniform rejection of the whole strip (interval bound widened
+          // by the strip's largest vertex uncertainty and a relative margin)
+          const float wmu = fmaf(S.r, W_e, S.mu0 + u * (2.0f * (fabsf(W_tx0) + fabsf(W_tx1) +
+                                                                fabsf(W_ty0) + fabsf(W_ty1) +
+                                                                fabsf(S.px) + fabsf(S.py)) +
+                                                         4.0f * S.r * W_l));
+          const float bx0 = fmaf(-S.r, W_ax1, W_tx0), bx1 = fmaf(-S.r, W_ax0, W_tx1);
+          const float by0 = fmaf(-S.r, W_ay1, W_ty0), by1 = fmaf(-S.r, W_ay0, W_ty1);
+          if (!W_any || S.px < bx0 - wmu || S.px > bx1 + wmu || S.py < by0 - wmu ||
+              S.py > by1 + wmu)
+            continue;
+        }
         const float dl = xl - S.px, dr = xr - S.px, db = yb - S.py, dt = yt - S.py;
         // relative mapped vertices beta_v - P = (theta_v - P) - r alpha_v
         const float a00x = fmaf(-S.r, v00.x, dl), a00y = fmaf(-S.r, v00.y, db);

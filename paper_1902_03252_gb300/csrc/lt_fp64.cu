@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kPrepThreads)
     p.a = v[LT_ROW_RCORE];
     p.sc = v[LT_ROW_RCUT];
     p.scale = kind == LT_PIEMD ? p.b0 * (p.sc / (p.sc - p.a)) : 0.0;
-    p.pad0 = p.pad1 = p.pad2 = 0.0;
+    p.sv = v[LT_ROW_SIGMA];
+    p.pad1 = p.pad2 = 0.0;
     p64[k] = p;
     atomicAdd(&cnt[kind], 1);
   }
@@ -346,43 +347,7 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
   return cudaGetLastError();
 }
 
-// ------------------------------------------------- FP64 point deflections
-// Deflection at up to 3 points by one warp: lanes evaluate potentials of a
-// 32-potential chunk in parallel into shared memory, then lane p sums point
-// p's contributions sequentially in potential index order.
 constexpr int kWarpsPerBlock64 = 4;
-
-__device__ void warp_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts, const double* px,
-                             const double* py, double* ax, double* ay, double2* buf /*[3][32]*/) {
-  const int lane = threadIdx.x & 31;
-  double sx = 0.0, sy = 0.0;
-  for (int c0 = 0; c0 < n_pot; c0 += 32) {
-    const int k = c0 + lane;
-    if (k < n_pot) {
-      const Pot64 p = pb[k];
-      for (int q = 0; q < npts; ++q) {
-        double kx, ky;
-        alpha64_one(p, px[q], py[q], kx, ky);
-        buf[q * 32 + lane] = make_double2(kx, ky);
-      }
-    }
-    __syncwarp();
-    if (lane < npts) {
-      const int cn = min(32, n_pot - c0);
-      for (int m = 0; m < cn; ++m) {
-        double2 v = buf[lane * 32 + m];
-        sx = sx + v.x;
-        sy = sy + v.y;
-      }
-    }
-    __syncwarp();
-  }
-  if (lane < npts) {
-    ax[lane] = sx;
-    ay[lane] = sy;
-  }
-  __syncwarp();
-}
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock64)
     k_resolve64(const Pot64* __restrict__ pot64, int n_pot, const SampleGrid* __restrict__ grids,

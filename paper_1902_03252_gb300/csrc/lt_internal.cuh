@@ -32,7 +32,7 @@ constexpr float kU32 = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
 // alpha64_one, so it reproduces an FP64 reference that follows the same
 // statement up to the ulps of the transcendental functions.
 struct Pot64 {
-  double kind, cx, cy, c, s, b0, e, q, k2, q2, a, sc, scale, pad0, pad1, pad2;
+  double kind, cx, cy, c, s, b0, e, q, k2, q2, a, sc, scale, sv, pad1, pad2;
 };
 static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 
@@ -126,19 +126,80 @@ __device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, 
   ay = gy * p.c + gx * p.s;
 }
 
-// ---------------------------------------------------- FP32 special functions
-// atan(t)/t and atanh(t)/t of t2 = t*t >= 0 in FP32 (CUDA atanf / log1pf,
-// <= 2 ulp; Taylor branch below 1e-8).
-__device__ __forceinline__ float atanc_sq32(float t2) {
-  float t = sqrtf(t2);
-  float r = atanf(t) / t;
-  return t2 < 1e-8f ? 1.0f - t2 * (1.0f / 3.0f) : r;
+// ------------------------------------------------- FP64 point deflections
+// Deflection at up to 3 points by one warp: lanes evaluate potentials of a
+// 32-potential chunk in parallel into shared memory, then lane p sums point
+// p's contributions sequentially in potential index order.
+__device__ inline void warp_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts, const double* px,
+                             const double* py, double* ax, double* ay, double2* buf /*[3][32]*/) {
+  const int lane = threadIdx.x & 31;
+  double sx = 0.0, sy = 0.0;
+  for (int c0 = 0; c0 < n_pot; c0 += 32) {
+    const int k = c0 + lane;
+    if (k < n_pot) {
+      const Pot64 p = pb[k];
+      for (int q = 0; q < npts; ++q) {
+        double kx, ky;
+        alpha64_one(p, px[q], py[q], kx, ky);
+        buf[q * 32 + lane] = make_double2(kx, ky);
+      }
+    }
+    __syncwarp();
+    if (lane < npts) {
+      const int cn = min(32, n_pot - c0);
+      for (int m = 0; m < cn; ++m) {
+        double2 v = buf[lane * 32 + m];
+        sx = sx + v.x;
+        sy = sy + v.y;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane < npts) {
+    ax[lane] = sx;
+    ay[lane] = sy;
+  }
+  __syncwarp();
 }
+
+
+// ---------------------------------------------------- FP32 special functions
+// atan(t)/t of t2 = t*t >= 0, branch-free: for t2 <= 1 a degree-8 polynomial
+// in t2 (least-squares fit at Chebyshev nodes, relative error < 1e-7; the
+// coefficients come from csrc/fit_poly.py); for t2 > 1, atan(t) = pi/2 -
+// atan(1/t) gives (pi/2)/t - P(1/t2)/t2.  One MUFU rsqrt.
+__device__ __forceinline__ float atanc_sq32(float t2) {
+  const float r = rsqrtf(t2);  // 1/t (infinite at t2 = 0, then unused)
+  const float inv = r * r;     // 1/t2
+  const bool big = t2 > 1.0f;
+  const float u = big ? inv : t2;
+  float p = 2.781707901e-03f;
+  p = fmaf(p, u, -1.579383570e-02f);
+  p = fmaf(p, u, 4.224103530e-02f);
+  p = fmaf(p, u, -7.465778757e-02f);
+  p = fmaf(p, u, 1.062265347e-01f);
+  p = fmaf(p, u, -1.419891983e-01f);
+  p = fmaf(p, u, 1.999201744e-01f);
+  p = fmaf(p, u, -3.333304396e-01f);
+  p = fmaf(p, u, 9.999999824e-01f);
+  return big ? fmaf(1.57079633f, r, -(p * inv)) : p;
+}
+// atanh(t)/t of t2 = t*t in [0, 1), branch-free: for t2 <= 1/4 a degree-5
+// polynomial in t2 (same fit, relative error < 1.1e-7); above,
+// atanh(t) = ln((1+t)/(1-t))/2 with MUFU rsqrt, rcp and lg2 (the ratio is
+// >= 3 there, where lg2 has a 2-ulp relative error).
 __device__ __forceinline__ float atanhc_sq32(float t2) {
-  // atanh(t) = 0.5 log1p(2t / (1 - t))
-  float t = sqrtf(t2);
-  float r = 0.5f * log1pf(2.0f * t / (1.0f - t)) / t;
-  return t2 < 1e-8f ? 1.0f + t2 * (1.0f / 3.0f) : r;
+  t2 = fminf(t2, 0.99999988f);
+  float p = 1.832424287e-01f;
+  p = fmaf(p, t2, 8.136755977e-02f);
+  p = fmaf(p, t2, 1.469695817e-01f);
+  p = fmaf(p, t2, 1.997503703e-01f);
+  p = fmaf(p, t2, 3.333387857e-01f);
+  p = fmaf(p, t2, 9.999999809e-01f);
+  const float r = rsqrtf(t2);  // 1/t
+  const float t = t2 * r;
+  const float l = __log2f(__fdividef(1.0f + t, 1.0f - t)) * (0.5f * 0.693147181f) * r;
+  return t2 > 0.25f ? l : p;
 }
 
 // Launch-shape variants of the FP32 deflection kernel (autotuned).
@@ -169,6 +230,11 @@ struct Work64 {
   int64_t tri;
   int32_t type;  // 0 = ambiguous pair, 1 = refine a certain hit
   int32_t pad;
+};
+
+// Adjoint point: position and the 2-vector coefficient of d alpha there.
+struct AdjPt {
+  double x, y, cx, cy;
 };
 
 // Hit record kept between the search and the chi^2 kernels.
@@ -223,6 +289,10 @@ cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_coun
                              int64_t* n_out, uint32_t* status, cudaStream_t st);
 cudaError_t launch_barycentres(const Pot64* pot64, int n_pot, int batch, const lt_obs& obs,
                                double* beta_obs, double* bary, cudaStream_t st);
+cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const SampleGrid* grids,
+                           const Hit* hits, int64_t hit_cap, const lt_obs& obs,
+                           const int32_t* match_hit, double2* lam, AdjPt* pts, double* grad,
+                           int sm_count, cudaStream_t st);
 cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, int n_samples,
                         int64_t hit_cap, int sample_base, const SampleGrid* grids,
                         const lt_obs& obs, double* chi2, int64_t* match_tri, int32_t* match_hit,

@@ -256,3 +256,77 @@ def test_edge_cases(oracle):
         m.deflect_grid((0.0, 0.0, -1.0, 1.0, 4, 4))
     with pytest.raises(lt.LTError):
         m.deflect_grid((0.0, 0.0, 1.0, 1.0, 4, 4), sample=3)
+
+
+# ---------------------------------------------------------------- gradient
+def grad_close(g, ref):
+    """1e-3 relative per component, with a floor of 1e-6 of the largest
+    component of the same sample (components that cancel to ~0)."""
+    floor = 1e-6 * np.abs(ref).max()
+    err = np.abs(g - ref)
+    return np.all(err <= 1e-3 * np.abs(ref) + floor), (err / (np.abs(ref) + floor)).max()
+
+
+@pytest.mark.parametrize("prec", [lt.MIXED, lt.FP64])
+def test_gradient_matches_oracle_c4(oracle, prec):
+    """d chi^2 / d(x, y, e, phi, r_core, sigma_v) of 100 PIEMD on the 1000^2
+    grid with 20 systems: the adjoint against the oracle's dual-number
+    gradient (same frozen assignment)."""
+    w = W.c4()
+    o = load_obs("c4")
+    obs = lt.Observations.from_dict(o)
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    grid = w.grids[0].as_tuple()
+    c2, g = m.chi2_grad([grid], obs, precision=prec)
+    assert m.sync()[0] == lt.LT_OK
+    mt, _, _ = m.last_matches(len(o["x"]), len(o["dls_ds"]))
+    mt = mt.cpu().numpy()[0]
+    ref = oracle.chi2(w.params[0], grid, o, n_threads=4)
+    assert np.array_equal(mt, ref["match_tri"])
+    rc, rg = oracle.chi2_grad(w.params[0], grid, o, ref["match_tri"])
+    ok, worst = grad_close(g.cpu().numpy()[0], rg)
+    print(f"gradient worst relative error {worst:.3g}")
+    assert ok, worst
+
+
+def test_gradient_matches_central_differences(oracle):
+    """The adjoint against FP64 central differences (h = 1e-6 relative) of the
+    oracle's frozen-assignment chi^2 on a small mixed-kind model."""
+    p = mixed_cluster(21, n_pot=12, half=15.0)
+    grid = (-25.0, -25.0, 50.0 / 249, 50.0 / 249, 250, 250)
+    rng = np.random.default_rng(21)
+    xy, sys, rs = [], [], []
+    while len(rs) < 4:
+        src, r = rng.uniform(-5, 5, 2), rng.uniform(0.4, 0.9)
+        H, _ = oracle.find_images(p, grid, [src], [r])
+        if len(H) < 2:
+            continue
+        for h in H:
+            xy.append((h["x"] + rng.normal(0, 0.01), h["y"] + rng.normal(0, 0.01)))
+            sys.append(len(rs))
+        rs.append(r)
+    xy = np.array(xy)
+    o = dict(x=xy[:, 0], y=xy[:, 1], sigma=np.full(len(xy), 0.01), sys=np.array(sys),
+             dls_ds=np.array(rs))
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    c2, g = m.chi2_grad([grid], lt.Observations.from_dict(o), precision=lt.MIXED)
+    assert m.sync()[0] == lt.LT_OK
+    mt = m.last_matches(len(xy), len(rs))[0].cpu().numpy()[0]
+    g = g.cpu().numpy()[0]
+    fd = np.zeros_like(g)
+    for k in range(p.shape[1]):
+        for c, row in enumerate([1, 2, 3, 4, 5, 7]):
+            if p[0, k] == W.SIS and row in (3, 4, 5):
+                continue
+            if p[0, k] == W.SIE and row == 5:
+                continue
+            h = 1e-6 * max(abs(p[row, k]), 1e-2)
+            pp, pm = p.copy(), p.copy()
+            pp[row, k] += h
+            pm[row, k] -= h
+            fd[k, c] = (oracle.chi2_frozen(pp, grid, o, mt) - oracle.chi2_frozen(pm, grid, o, mt)) / (2 * h)
+    ok, worst = grad_close(g, fd)
+    print(f"adjoint vs central differences: worst relative error {worst:.3g}")
+    assert ok, worst
