@@ -229,6 +229,30 @@ typedef struct {
 lt_status lt_profile_enable(lt_model* model, int on);
 lt_status lt_profile_read(lt_model* model, lt_profile* out, int reset);
 
+/* Allocation-free deflection grid, for callers that cannot allocate device
+ * memory (code inside an allocator hook or memory-pool callback, plugins of
+ * an application that owns every device allocation, processes that reserve
+ * all device memory at start-up).  The paper has no counterpart: it is an
+ * integration variant of lt_deflect_grid in mixed precision for one lens
+ * model, and needs no lt_model.
+ * params: device, float64 [LT_N_ROWS][n_pot] (the layout of one sample of
+ * lt_model_set_params), 1 <= n_pot <= 4096.  grid: host.  alpha_out: device
+ * [ny][nx][2] float; err_out: optional device [ny][nx] float (the FP32
+ * running error bound); status_out: optional device int32 receiving LT_OK or
+ * LT_ERR_NONFINITE (invalid parameters, which are neutralised to zero mass).
+ * Returns LT_ERR_INVALID_ARG for null pointers, a bad grid or n_pot outside
+ * [1, 4096]; LT_ERR_CUDA if a runtime call fails.
+ * Its scratch is a fixed file-scope device array of about 0.8 MiB that every
+ * GPU loading the library holds until exit; the call itself allocates
+ * nothing.  The first call on a device resolves that array's address
+ * (cudaGetSymbolAddress, with the device current): make that first call
+ * before any stream capture.  All calls on a device share the array, so
+ * calls that overlap on the GPU (different streams, or threads) race; order
+ * them on one stream. */
+lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot, const lt_grid* grid,
+                                  float* alpha_out, float* err_out, int32_t* status_out,
+                                  uintptr_t stream);
+
 /* Library version string. */
 const char* lt_version(void);
 

@@ -27,6 +27,7 @@ PER_FILE = {
     # flush-to-zero the MUFU approximations (rsqrt, rcp, lg2) are single
     # instructions instead of range-checked sequences
     "lt_fp32.cu": ["-ftz=true"],
+    "lt_noalloc.cu": ["-ftz=true"],
     "lt_api.cu": [],
 }
 

@@ -1,0 +1,186 @@
+// lt_deflect_grid_noalloc: the mixed-precision deflection grid of one lens
+// model for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc at all: code running inside a host
+// allocator hook or a memory-pool callback, plugins of applications that own
+// every allocation on the device, and processes that pre-reserve all device
+// memory at start-up.  This entry point serves them: it needs no model and no
+// workspace.  Its scratch -- the prepared potential records, the kind
+// segments and a status word -- lives in one file-scope device array of fixed
+// size (kNoallocBytes, about 0.8 MiB), which every GPU that loads the library
+// holds until the process exits.  The caller still passes the parameters and
+// the output buffers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "lt_fp32.cuh"
+#include "lt_internal.cuh"
+
+namespace lt {
+namespace {
+
+constexpr int kNoallocMaxPot = 4096;  // largest model this entry point accepts
+constexpr size_t kOffPot64 = 0;
+constexpr size_t kOffPot32 = kOffPot64 + sizeof(Pot64) * kNoallocMaxPot;
+constexpr size_t kOffSeg = kOffPot32 + sizeof(Pot32) * kNoallocMaxPot;
+constexpr size_t kOffStatus = kOffSeg + 256;
+constexpr size_t kNoallocBytes = kOffStatus + 256;
+
+// The scratch.  In host code this name is only a stand-in for the symbol: the
+// device address must be obtained with cudaGetSymbolAddress on each device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
+
+// Resolve the scratch address and SM count once per device (the device must
+// be current).  Neither call allocates.
+lt_status device_setup(int dev, unsigned char** base, int* sms) {
+  if (dev < 0 || dev >= kMaxDevices) return LT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LT_ERR_CUDA;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return LT_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+    g_sm_count[dev] = n;
+  }
+  *base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  *sms = g_sm_count[dev];
+  return LT_OK;
+}
+
+constexpr int kNT = 256, kNPT = 4;
+
+// Same arithmetic as the batched deflection kernel (same per-potential
+// functions, kind segments and order), for one sample, writing alpha and the
+// running error bound straight into the caller's buffers.
+__global__ void __launch_bounds__(kNT)
+    k_deflect32_noalloc(const Pot32* __restrict__ pot32, const Seg32* __restrict__ seg, int n_pot,
+                        SampleGrid g, int64_t n_items, float2* __restrict__ alpha,
+                        float* __restrict__ err) {
+  __shared__ float4 sp[256 * 5];
+  const Seg32 sg = *seg;
+  const int64_t nodes = (int64_t)g.nx * g.ny;
+  const float x0 = (float)g.x0, y0 = (float)g.y0, hx = (float)g.dx, hy = (float)g.dy;
+  const float theta4 = 4.0f * g.theta_max;
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int64_t base = item * (int64_t)(kNT * kNPT);
+    float X[kNPT], Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
+#pragma unroll
+    for (int m = 0; m < kNPT; ++m) {
+      int64_t n = base + m * kNT + threadIdx.x;
+      if (n >= nodes) n = nodes - 1;
+      const int j = (int)(n / g.nx);
+      const int i = (int)(n - (int64_t)j * g.nx);
+      X[m] = fmaf((float)i, hx, x0);
+      Y[m] = fmaf((float)j, hy, y0);
+      AX[m] = 0.0f;
+      AY[m] = 0.0f;
+      ER[m] = 0.0f;
+    }
+    for (int c0 = 0; c0 < n_pot; c0 += 256) {
+      const int cn = min(256, n_pot - c0);
+      __syncthreads();
+      for (int v = threadIdx.x; v < cn * 5; v += kNT) {
+        const int k = v / 5, w = v - k * 5;
+        float4 val = pot32[c0 + k].f[w];
+        if (w == 4) {
+          const float4 h = pot32[c0 + k].f[0];
+          val.x = val.x * (theta4 + fabsf(h.x) + fabsf(h.y));
+        }
+        sp[v] = val;
+      }
+      __syncthreads();
+      const int e_sis = min(max(sg.n_sis - c0, 0), cn);
+      const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
+      for (int k = 0; k < e_sis; ++k) {
+#pragma unroll
+        for (int m = 0; m < kNPT; ++m) sis32(&sp[k * 5], sp[k * 5 + 4].x, X[m], Y[m], AX[m], AY[m], ER[m]);
+      }
+      for (int k = e_sis; k < e_pie; ++k) {
+#pragma unroll
+        for (int m = 0; m < kNPT; ++m)
+          piemd32(&sp[k * 5], sp[k * 5 + 4].x, X[m], Y[m], AX[m], AY[m], ER[m]);
+      }
+      for (int k = e_pie; k < cn; ++k) {
+#pragma unroll
+        for (int m = 0; m < kNPT; ++m) sie32(&sp[k * 5], sp[k * 5 + 4].x, X[m], Y[m], AX[m], AY[m], ER[m]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < kNPT; ++m) {
+      const int64_t n = base + m * kNT + threadIdx.x;
+      if (n < nodes) {
+        alpha[n] = make_float2(AX[m], AY[m]);
+        if (err) err[n] = 2.0f * kU32 * (ER[m] + sg.q_tot);
+      }
+    }
+  }
+}
+
+__global__ void k_noalloc_status(const uint32_t* st, int32_t* out) {
+  *out = (*st & ST_NONFINITE) ? (int32_t)LT_ERR_NONFINITE : (int32_t)LT_OK;
+}
+
+}  // namespace
+}  // namespace lt
+
+using namespace lt;
+
+extern "C" lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot,
+                                             const lt_grid* grid, float* alpha_out,
+                                             float* err_out, int32_t* status_out,
+                                             uintptr_t stream) {
+  if (!params || !grid || !alpha_out) return LT_ERR_INVALID_ARG;
+  if (n_pot < 1 || n_pot > kNoallocMaxPot) return LT_ERR_INVALID_ARG;
+  const lt_grid& gr = *grid;
+  if (gr.nx < 1 || gr.ny < 1 || !std::isfinite(gr.x0) || !std::isfinite(gr.y0) ||
+      !std::isfinite(gr.dx) || !std::isfinite(gr.dy) || !(gr.dx > 0) || !(gr.dy > 0))
+    return LT_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LT_ERR_CUDA;
+  unsigned char* base = nullptr;
+  int sms = 1;
+  lt_status s = device_setup(dev, &base, &sms);
+  if (s != LT_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Pot64* p64 = reinterpret_cast<Pot64*>(base + kOffPot64);
+  Pot32* p32 = reinterpret_cast<Pot32*>(base + kOffPot32);
+  Seg32* seg = reinterpret_cast<Seg32*>(base + kOffSeg);
+  uint32_t* status = reinterpret_cast<uint32_t*>(base + kOffStatus);
+  // the status word keeps the previous call's value: clear it first
+  if (cudaMemsetAsync(status, 0, sizeof(uint32_t), st) != cudaSuccess) return LT_ERR_CUDA;
+  if (launch_prep(params, 1, n_pot, p64, p32, seg, status, st) != cudaSuccess) return LT_ERR_CUDA;
+  SampleGrid g;
+  g.x0 = gr.x0; g.y0 = gr.y0; g.dx = gr.dx; g.dy = gr.dy; g.nx = gr.nx; g.ny = gr.ny;
+  g.node_off = 0;
+  const double tm = std::fmax(std::fmax(std::fabs(gr.x0), std::fabs(gr.x0 + (gr.nx - 1) * gr.dx)),
+                              std::fmax(std::fabs(gr.y0), std::fabs(gr.y0 + (gr.ny - 1) * gr.dy)));
+  g.theta_max = (float)(tm * (1.0 + 1e-6));
+  g.pad = 0.f;
+  const int64_t nodes = (int64_t)gr.nx * gr.ny;
+  const int64_t n_items = (nodes + kNT * kNPT - 1) / (kNT * kNPT);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32_noalloc, kNT, 0) !=
+      cudaSuccess)
+    return LT_ERR_CUDA;
+  int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if (blocks > n_items) blocks = n_items;
+  k_deflect32_noalloc<<<(unsigned)blocks, kNT, 0, st>>>(p32, seg, n_pot, g, n_items,
+                                                        reinterpret_cast<float2*>(alpha_out),
+                                                        err_out);
+  if (cudaGetLastError() != cudaSuccess) return LT_ERR_CUDA;
+  if (status_out) {
+    k_noalloc_status<<<1, 1, 0, st>>>(status, status_out);
+    if (cudaGetLastError() != cudaSuccess) return LT_ERR_CUDA;
+  }
+  return LT_OK;
+}
