@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the HFF deflection and batched measurements")
     return ap.parse_args()
 
 
@@ -367,6 +369,9 @@ def run_ours(a, rank, world, local):
         "wall_s_timed_region": wall,
         "deflect32_source_sha256": source_sha(DEFLECT32_SOURCES),
     }
+    if not a.no_extras:
+        line["hff_deflection"] = extra_hff(lt, W, torch, dev)
+        line["batched_c3"] = extra_batched(lt, W, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(w, o)
     if rank == 0:
@@ -374,6 +379,69 @@ def run_ours(a, rank, world, local):
     m.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def extra_hff(lt, W, torch, dev, steps=3):
+    """The paper's benchmark (Sect. 4): deflection of 6730^2 pixels at 0.03"
+    by 2 cluster + 700 galaxy SIE, FP32 (with its running bound) and FP64."""
+    w = W.hff()
+    grid = w.grids[0].as_tuple()
+    n = w.grids[0].nx
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    a32 = torch.empty((n, n, 2), dtype=torch.float32, device=dev)
+
+    def time_it(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k / 1e3
+
+    t32 = time_it(lambda: m.deflect_grid(grid, precision=lt.MIXED), steps)
+    del a32
+    t64 = time_it(lambda: m.deflect_grid(grid, precision=lt.FP64), 1)
+    m.close()
+    npot = w.grids[0].nodes * w.n_pot
+    return {"workload": "6730^2 pixels at 0.03\", 2 cluster + 700 galaxy SIE (Sect. 4)",
+            "node_pot": npot, "fp32_s": t32, "fp64_s": t64,
+            "fp32_node_pot_per_s": npot / t32, "fp64_node_pot_per_s": npot / t64,
+            "paper_s": {"V100": {"dp": 0.46, "mixed": 0.39}, "P100": {"dp": 0.71, "mixed": 0.58},
+                        "GTX1080Ti": {"dp": 6.8, "mixed": 1.58}, "Xeon12c": {"dp": 8.1, "mixed": 7.40}},
+            "note": "deflection grid only, as timed in the paper; FP32 here is the full grid with "
+                    "its per-node error bound, the paper's mixed form recomputes DP patches"}
+
+
+def extra_batched(lt, W, torch, dev, steps=2):
+    """1024 perturbed 50-PIEMD samples on grids of 500^2..2000^2, 10 systems,
+    one chi^2 per sample, whole batch per call through the CUDA-graph path."""
+    w = W.c3()
+    with open(os.path.join(ROOT, "tests", "golden", "obs_c3.json")) as f:
+        o = json.load(f)
+    grids = [g.as_tuple() for g in w.grids]
+    m = lt.Model(w.n_pot, w.batch)
+    m.set_params(w.params)
+    obs = lt.Observations.from_dict(o, device=dev)
+    out = torch.empty(w.batch, dtype=torch.float64, device=dev)
+    m.chi2(grids, obs, precision=lt.MIXED, out=out, graph=True)
+    st, stats = m.sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        m.chi2(grids, obs, precision=lt.MIXED, out=out, graph=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / steps / 1e3
+    npot = w.node_pot()
+    m.close()
+    return {"workload": "c3: 1024 samples x 50 PIEMD, grids 500^2..2000^2, 10 systems",
+            "s_per_batch": t, "chi2_evals_per_s": w.batch / t, "node_pot_per_s": npot / t,
+            "status": int(st), "stats": stats}
 
 
 def main():

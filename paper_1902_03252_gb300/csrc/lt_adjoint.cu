@@ -32,25 +32,22 @@ constexpr int kAdjThreads = 128;
 constexpr int kAdjChunk = 256;
 
 // ------------------------------------------------------------ coefficients
-// Pass 1, one warp per (sample, observed image m): if m is the first observed
+// Pass 1, one block per (sample, observed image m): if m is the first observed
 // image matched to its predicted image h, build h's three vertex points.  The
-// vertex deflections are recomputed in FP64 (lanes split the potentials,
+// vertex deflections are recomputed in FP64 (threads split the potentials,
 // sums in index order): M = [beta_B - beta_A, beta_C - beta_A] is a
 // difference of large deflections and its FP32 rounding would be amplified
 // by M's conditioning in magnified triangles.
-constexpr int kAdjWarps = 4;
+constexpr int kAdjHitThreads = 128;
 
-__global__ void __launch_bounds__(32 * kAdjWarps)
+__global__ void __launch_bounds__(kAdjHitThreads)
     k_adj_hits(const Pot64* __restrict__ pot64, int n_pot, int batch,
                const SampleGrid* __restrict__ grids, const Hit* __restrict__ hits,
                int64_t hit_cap, lt_obs obs, const int32_t* __restrict__ match_hit,
                double2* __restrict__ lam, AdjPt* __restrict__ pts, int P) {
-  __shared__ double2 buf[kAdjWarps][3 * 32];
-  __shared__ double res[kAdjWarps][6];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * kAdjWarps;
-  for (int64_t f = (int64_t)blockIdx.x * kAdjWarps + wid; f < (int64_t)batch * obs.n_obs;
-       f += nw) {
+  __shared__ double2 buf[3 * kAdjHitThreads];
+  __shared__ double res[6];
+  for (int64_t f = blockIdx.x; f < (int64_t)batch * obs.n_obs; f += gridDim.x) {
     const int b = (int)(f / obs.n_obs);
     const int m = (int)(f - (int64_t)b * obs.n_obs);
     const int32_t* mh = match_hit + (int64_t)b * obs.n_obs;
@@ -58,9 +55,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps)
     const int h = mh[m];
     bool owner = h >= 0;
     for (int k = 0; k < m && owner; ++k) owner = mh[k] != h;
-    if (!owner) {  // warp-uniform
-      if (lane < 3) pp[3 * m + lane] = AdjPt{0.0, 0.0, 0.0, 0.0};
-      if (lane == 0) lam[f] = make_double2(0.0, 0.0);
+    if (!owner) {  // block-uniform
+      if (threadIdx.x < 3) pp[3 * m + threadIdx.x] = AdjPt{0.0, 0.0, 0.0, 0.0};
+      if (threadIdx.x == 0) lam[f] = make_double2(0.0, 0.0);
       continue;
     }
     const SampleGrid g = grids[b];
@@ -76,9 +73,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps)
       TX[v] = g.x0 + (double)(i + di[v]) * g.dx;
       TY[v] = g.y0 + (double)(j + dj[v]) * g.dy;
     }
-    warp_alpha64(pot64 + (int64_t)b * n_pot, n_pot, 3, TX, TY, &res[wid][0], &res[wid][3],
-                 buf[wid]);
-    if (lane == 0) {
+    block_alpha64<kAdjHitThreads>(pot64 + (int64_t)b * n_pot, n_pot, 3, TX, TY, &res[0],
+                                  &res[3], buf);
+    if (threadIdx.x == 0) {
       // dchi^2/dx of this predicted image, over every observed image matched to it
       double Gx = 0.0, Gy = 0.0;
       for (int k = m; k < obs.n_obs; ++k) {
@@ -90,8 +87,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps)
       const double r = obs.dls_ds[obs.sys[m]];
       double BX[3], BY[3];
       for (int v = 0; v < 3; ++v) {
-        BX[v] = TX[v] - r * res[wid][v];
-        BY[v] = TY[v] - r * res[wid][3 + v];
+        BX[v] = TX[v] - r * res[v];
+        BY[v] = TY[v] - r * res[3 + v];
       }
       const double M00 = BX[1] - BX[0], M01 = BX[2] - BX[0];
       const double M10 = BY[1] - BY[0], M11 = BY[2] - BY[0];
@@ -105,7 +102,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps)
       for (int v = 0; v < 3; ++v)
         pp[3 * m + v] = AdjPt{TX[v], TY[v], r * H.w[v] * lx, r * H.w[v] * ly};
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -302,9 +299,9 @@ cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const Sampl
                            int sm_count, cudaStream_t st) {
   const int P = 4 * obs.n_obs;
   const int64_t warps = (int64_t)batch * obs.n_obs;
-  int64_t blocks = (warps + kAdjWarps - 1) / kAdjWarps;
+  int64_t blocks = warps;
   if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
-  k_adj_hits<<<(unsigned)blocks, 32 * kAdjWarps, 0, st>>>(pot64, n_pot, batch, grids, hits,
+  k_adj_hits<<<(unsigned)blocks, kAdjHitThreads, 0, st>>>(pot64, n_pot, batch, grids, hits,
                                                           hit_cap, obs, match_hit, lam, pts, P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -66,6 +66,12 @@ struct lt_model {
   SampleGrid* d_plan_grids = nullptr;
   int64_t* d_plan_items = nullptr;
   size_t plan_items_alloc = 0;
+  // dynamic item counters: [0] single-grid calls, then (deflect, search) per chunk
+  unsigned long long* d_sched = nullptr;
+  size_t sched_alloc = 0;
+  // side stream for the barycentres, overlapping the FP32 deflection
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Plan plan;
   // chi^2 intermediates
   double* d_beta_obs = nullptr;
@@ -245,6 +251,8 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
   }
   lt_status s = grow(m, &m->d_plan_items, &m->plan_items_alloc, items.size());
   if (s != LT_OK) return s;
+  s = grow(m, &m->d_sched, &m->sched_alloc, 1 + 2 * p.chunks.size());
+  if (s != LT_OK) return s;
   LT_CUDA(cudaMemcpyAsync(m->d_plan_grids, sg.data(), sizeof(SampleGrid) * n,
                           cudaMemcpyHostToDevice, st));
   LT_CUDA(cudaMemcpyAsync(m->d_plan_items, items.data(), sizeof(int64_t) * items.size(),
@@ -324,8 +332,11 @@ lt_status prepare(lt_model* m, const lt_grid* grids, int precision, int64_t hit_
 }
 
 // Deflection + search (+ FP64 resolution) of one chunk into the hit lists.
-lt_status enqueue_search(lt_model* m, const Chunk& c, int precision, Sources src, int64_t hit_cap,
-                         cudaStream_t st) {
+lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int64_t hit_cap,
+                         cudaStream_t st, cudaEvent_t wait_before_search) {
+  const Chunk& c = m->plan.chunks[ci];
+  unsigned long long* next_defl = m->d_sched + 1 + 2 * ci;
+  unsigned long long* next_search = next_defl + 1;
   const int nb = c.b1 - c.b0;
   const SampleGrid* g = m->d_plan_grids + c.b0;
   const int64_t* di = m->d_plan_items + c.defl_off;
@@ -345,6 +356,7 @@ lt_status enqueue_search(lt_model* m, const Chunk& c, int precision, Sources src
       LT_CUDA(launch_deflect64(m->d_pot64 + (size_t)c.b0 * m->n_pot, m->n_pot, g, di, nb,
                                c.defl_items, nodes, m->sm_count, st));
     }
+    if (wait_before_search) LT_CUDA(cudaStreamWaitEvent(st, wait_before_search, 0));
     ProfScope ps(m, st, 1);
     LT_CUDA(launch_search64(nodes, g, si, nb, c.search_items, src, hits, hit_cap, hc,
                             m->d_counters, m->d_status, m->sm_count, st));
@@ -353,12 +365,15 @@ lt_status enqueue_search(lt_model* m, const Chunk& c, int precision, Sources src
     {
       ProfScope ps(m, st, 0, np, 0);
       LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)c.b0 * m->n_pot, m->d_seg + c.b0, m->n_pot,
-                               g, di, nb, c.defl_items, m->shape, nodes, m->sm_count, st));
+                               g, di, nb, c.defl_items, m->shape, nodes, next_defl,
+                               m->sm_count, st));
     }
+    if (wait_before_search) LT_CUDA(cudaStreamWaitEvent(st, wait_before_search, 0));
     {
       ProfScope ps(m, st, 1);
       LT_CUDA(launch_search32(nodes, g, si, nb, c.search_items, src, hits, hit_cap, work,
-                              m->work_cap, hc, wc, m->d_counters, m->d_status, m->sm_count, st));
+                              m->work_cap, hc, wc, m->d_counters, m->d_status, next_search,
+                              m->sm_count, st));
     }
     ProfScope ps(m, st, 2);
     LT_CUDA(launch_resolve64(m->d_pot64, m->n_pot, g, src, work, wc, nb, m->work_cap, hits,
@@ -369,6 +384,8 @@ lt_status enqueue_search(lt_model* m, const Chunk& c, int precision, Sources src
 
 lt_status reset_counts(lt_model* m, cudaStream_t st) {
   LT_CUDA(cudaMemsetAsync(m->d_counters, 0, sizeof(long long) * CNT_N, st));
+  if (m->d_sched)
+    LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long) * m->sched_alloc, st));
   LT_CUDA(cudaMemsetAsync(m->d_hit_count, 0, sizeof(unsigned long long) * m->batch, st));
   LT_CUDA(cudaMemsetAsync(m->d_work_count, 0, sizeof(unsigned long long) * m->batch, st));
   return LT_OK;
@@ -388,15 +405,21 @@ lt_status enqueue_chi2(lt_model* m, const lt_obs& obs, int precision, double* ch
                        cudaStream_t st) {
   lt_status s = reset_counts(m, st);
   if (s != LT_OK) return s;
+  // the barycentres need only the parameters: run them on the side stream,
+  // overlapping the first chunk's deflection; the search waits for them
+  LT_CUDA(cudaEventRecord(m->ev_fork, st));
+  LT_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
   {
-    ProfScope ps(m, st, 3);
+    ProfScope ps(m, m->side, 3);
     LT_CUDA(launch_barycentres(m->d_pot64, m->n_pot, m->batch, obs, m->d_beta_obs, m->d_bary,
-                               st));
+                               m->side));
   }
+  LT_CUDA(cudaEventRecord(m->ev_join, m->side));
   Sources src{m->d_bary, obs.dls_ds, obs.n_sys, 0, 0};
   const int64_t hc = m->hits_cap_alloc;
-  for (const Chunk& c : m->plan.chunks) {
-    s = enqueue_search(m, c, precision, src, hc, st);
+  for (size_t ci = 0; ci < m->plan.chunks.size(); ++ci) {
+    const Chunk& c = m->plan.chunks[ci];
+    s = enqueue_search(m, ci, precision, src, hc, st, ci == 0 ? m->ev_join : nullptr);
     if (s != LT_OK) return s;
     ProfScope ps(m, st, 3);
     LT_CUDA(launch_chi2(m->d_hits + (size_t)c.b0 * hc, m->d_hit_count + c.b0, c.b1 - c.b0, hc,
@@ -466,6 +489,11 @@ lt_status lt_model_create(const lt_model_desc* desc, lt_model** out) {
     return fail(e);
   if ((e = cudaMalloc(&m->d_plan_grids, sizeof(SampleGrid) * m->batch)) != cudaSuccess)
     return fail(e);
+  if ((e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e);
+  if ((e = cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e);
   if ((e = cudaMemset(m->d_status, 0, sizeof(uint32_t))) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(m->d_counters, 0, sizeof(long long) * CNT_N)) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(m->d_hit_count, 0, sizeof(unsigned long long) * m->batch)) != cudaSuccess)
@@ -489,11 +517,14 @@ void lt_model_destroy(lt_model* m) {
   void* ptrs[] = {m->d_params, m->d_pot64, m->d_pot32, m->d_seg, m->d_status, m->d_counters,
                   m->d_nodes, m->d_hits, m->d_work, m->d_hit_count, m->d_work_count,
                   m->d_plan_grids, m->d_plan_items, m->d_beta_obs, m->d_bary, m->d_match_tri,
-                  m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts};
+                  m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+  if (m->side) cudaStreamDestroy(m->side);
+  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+  if (m->ev_join) cudaEventDestroy(m->ev_join);
   for (auto& r : m->prof_pending) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);
@@ -563,9 +594,14 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
                              dev->items, 1, items[1], (double2*)alpha_out, m->sm_count, st));
   } else {
     float4* nodes4 = (float4*)base;
+    if (!m->d_sched) {
+      lt_status s2 = grow(m, &m->d_sched, &m->sched_alloc, 1);
+      if (s2 != LT_OK) return s2;
+    }
+    LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long), st));
     LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)sample * m->n_pot, m->d_seg + sample, m->n_pot,
-                             &dev->g, dev->items, 1, items[1], m->shape, nodes4, m->sm_count,
-                             st));
+                             &dev->g, dev->items, 1, items[1], m->shape, nodes4, m->d_sched,
+                             m->sm_count, st));
     LT_CUDA(launch_unpack32(nodes4, nodes, (float2*)alpha_out, err_out, st));
   }
   return LT_OK;
@@ -589,9 +625,10 @@ lt_status lt_find_images(lt_model* m, const lt_grid* grids, int32_t n_src, const
   if (s != LT_OK) return s;
   Sources src{src_xy, dls_ds, n_src, 1, 0};
   const int64_t hca = m->hits_cap_alloc;
-  for (const Chunk& c : m->plan.chunks) {
+  for (size_t ci = 0; ci < m->plan.chunks.size(); ++ci) {
+    const Chunk& c = m->plan.chunks[ci];
     if (n_src > 0) {
-      s = enqueue_search(m, c, precision, src, hca, st);
+      s = enqueue_search(m, ci, precision, src, hca, st, nullptr);
       if (s != LT_OK) return s;
     }
     LT_CUDA(launch_sort_hits(m->d_hits + (size_t)c.b0 * hca, m->d_hit_count + c.b0, c.b1 - c.b0,

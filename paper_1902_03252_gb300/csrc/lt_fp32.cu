@@ -33,29 +33,39 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
                                                   const SampleGrid* __restrict__ grids,
                                                   const int64_t* __restrict__ item_off,
                                                   int n_samples, int64_t n_items,
-                                                  float4* __restrict__ node_out) {
+                                                  float4* __restrict__ node_out,
+                                                  unsigned long long* __restrict__ next_item) {
   __shared__ float4 sp[kChunk32 * 5];
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  __shared__ long long s_item;
+  for (;;) {
+    // dynamic distribution of the equal-size work items: blocks that start
+    // late (another kernel still resident on their SM) simply take fewer
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= n_items) break;
     int b = find_sample(item_off, n_samples, item);
     const SampleGrid g = grids[b];
     const Seg32 sg = seg[b];
     const int64_t nodes = (int64_t)g.nx * g.ny;
     const int64_t base = (item - item_off[b]) * (int64_t)(NT * NPT);
-    const float x0 = (float)g.x0, y0 = (float)g.y0, hx = (float)g.dx, hy = (float)g.dy;
-    float X[NPT], Y[NPT], AX[NPT], AY[NPT], ER[NPT];
+        float X[NPT], Y[NPT], AX[NPT], AY[NPT], ER[NPT];
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
       int64_t n = base + m * NT + threadIdx.x;
       if (n >= nodes) n = nodes - 1;
       int j = (int)(n / g.nx);
       int i = (int)(n - (int64_t)j * g.nx);
-      X[m] = fmaf((float)i, hx, x0);
-      Y[m] = fmaf((float)j, hy, y0);
+      // node coordinates rounded once from FP64: error u|theta| (App. A's
+      // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
+      X[m] = (float)(g.x0 + (double)i * g.dx);
+      Y[m] = (float)(g.y0 + (double)j * g.dy);
       AX[m] = 0.0f;
       AY[m] = 0.0f;
       ER[m] = 0.0f;
     }
-    const float theta4 = 4.0f * g.theta_max;
+    const float theta1 = g.theta_max;
     const Pot32* pb = pot32 + (int64_t)b * n_pot;
     for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
       const int cn = min(kChunk32, n_pot - c0);
@@ -65,7 +75,7 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
         float4 val = pb[c0 + k].f[w];
         if (w == 4) {  // translation-error coefficient for this grid
           float4 h = pb[c0 + k].f[0];
-          val.x = val.x * (theta4 + fabsf(h.x) + fabsf(h.y));
+          val.x = val.x * (theta1 + fabsf(h.x) + fabsf(h.y));
         }
         sp[v] = val;
       }
@@ -107,7 +117,8 @@ template <int NT, int NPT>
 static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int n_pot,
                                       const SampleGrid* grids, const int64_t* item_off,
                                       int n_samples, int64_t n_items, float4* node_out,
-                                      int sm_count, cudaStream_t st) {
+                                      unsigned long long* next_item, int sm_count,
+                                      cudaStream_t st) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32<NT, NPT>, NT, 0);
   if (per_sm < 1) per_sm = 1;
@@ -115,23 +126,24 @@ static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int 
   if (blocks > n_items) blocks = n_items;
   if (blocks < 1) return cudaSuccess;
   k_deflect32<NT, NPT><<<(unsigned)blocks, NT, 0, st>>>(pot32, seg, n_pot, grids, item_off,
-                                                          n_samples, n_items, node_out);
+                                                          n_samples, n_items, node_out,
+                                                          next_item);
   return cudaGetLastError();
 }
 
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
                              const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, float4* node_out, int sm_count,
-                             cudaStream_t st) {
+                             int64_t n_items, int shape, float4* node_out,
+                             unsigned long long* next_item, int sm_count, cudaStream_t st) {
   switch (shape) {
     case 0: return launch_deflect32_t<256, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, sm_count, st);
+                                              n_items, node_out, next_item, sm_count, st);
     case 2: return launch_deflect32_t<128, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, sm_count, st);
+                                              n_items, node_out, next_item, sm_count, st);
     case 3: return launch_deflect32_t<128, 8>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, sm_count, st);
+                                              n_items, node_out, next_item, sm_count, st);
     default: return launch_deflect32_t<256, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                               n_items, node_out, sm_count, st);
+                                               n_items, node_out, next_item, sm_count, st);
   }
 }
 
@@ -156,7 +168,7 @@ cudaError_t launch_unpack32(const float4* nodes, int64_t n, float2* alpha, float
 
 // ---------------------------------------------------------- triangle search
 constexpr int kSearchThreads = 256;  // cells per work item (one per thread)
-constexpr int kMaxSrcSmem = 1024;    // sources staged in shared memory at a time
+constexpr int kMaxSrcSmem = 256;     // sources staged in shared memory at a time
 
 // Source data staged per sample: position relative coordinates use FP32.
 struct SrcSmem {
@@ -240,16 +252,41 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+struct StripBox {
+  float tx0, tx1, ty0, ty1, ax0, ax1, ay0, ay1, e, l;
+  int any, pad;
+};
+
+// One work item = 256 consecutive cells, 8 warps of 32 ("strips").  For each
+// chunk of sources: (1) every (strip, source) pair is tested once, by one
+// thread, against a conservative source-plane box of the strip,
+//   beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x]
+// (the same in y) widened by the strip's largest vertex uncertainty; the
+// surviving sources of each strip are compacted into a shared list; (2) each
+// warp runs the per-cell test only for its strip's survivors.  Most pairs
+// never reach the per-cell arithmetic.
 __global__ void __launch_bounds__(kSearchThreads)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
                Hit* __restrict__ hits, int64_t hit_cap, Work64* __restrict__ work,
                int64_t work_cap, unsigned long long* hit_count, unsigned long long* work_count,
-               long long* counters, uint32_t* status) {
+               long long* counters, uint32_t* status,
+               unsigned long long* __restrict__ next_item) {
+  constexpr int kStrips = kSearchThreads / 32;
   __shared__ SrcSmem ss[kMaxSrcSmem];
+  __shared__ StripBox sb[kStrips];
+  __shared__ unsigned short surv[kStrips][kMaxSrcSmem];
+  __shared__ int n_surv[kStrips];
+  __shared__ long long s_item;
   const float u = kU32;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   long long n_hit = 0, n_amb = 0, n_ref = 0;
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= n_items) break;
     const int b = find_sample(item_off, n_samples, item);
     const SampleGrid g = grids[b];
     const int sample = src.sample_base + b;
@@ -262,52 +299,66 @@ __global__ void __launch_bounds__(kSearchThreads)
     const int64_t n00 = g.node_off + (int64_t)j * g.nx + i;
     const float4 v00 = nodes[n00], v10 = nodes[n00 + 1], v01 = nodes[n00 + g.nx],
                  v11 = nodes[n00 + g.nx + 1];
-    const float xl = fmaf((float)i, (float)g.dx, (float)g.x0);
-    const float xr = fmaf((float)(i + 1), (float)g.dx, (float)g.x0);
-    const float yb = fmaf((float)j, (float)g.dy, (float)g.y0);
-    const float yt = fmaf((float)(j + 1), (float)g.dy, (float)g.y0);
+    const float hx = (float)g.dx, hy = (float)g.dy, gx0 = (float)g.x0, gy0 = (float)g.y0;
+    const float hmax = fmaxf(fabsf(hx), fabsf(hy));
+    const float xl = fmaf((float)i, hx, gx0);
+    const float xr = fmaf((float)(i + 1), hx, gx0);
+    const float yb = fmaf((float)j, hy, gy0);
+    const float yt = fmaf((float)(j + 1), hy, gy0);
     const float emax = fmaxf(fmaxf(v00.z, v10.z), fmaxf(v01.z, v11.z));
     const float l00 = fabsf(v00.x) + fabsf(v00.y), l10 = fabsf(v10.x) + fabsf(v10.y);
     const float l01 = fabsf(v01.x) + fabsf(v01.y), l11 = fabsf(v11.x) + fabsf(v11.y);
     const float lmax = fmaxf(fmaxf(l00, l10), fmaxf(l01, l11));
-    // Conservative source-plane box of the warp's 32 cells for any r > 0:
-    // beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x].
-    const float inf = __int_as_float(0x7f800000);
-    const float W_tx0 = warp_min(valid ? xl : inf), W_tx1 = warp_max(valid ? xr : -inf);
-    const float W_ty0 = warp_min(valid ? yb : inf), W_ty1 = warp_max(valid ? yt : -inf);
-    const float W_ax0 = warp_min(valid ? fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)) : inf);
-    const float W_ax1 = warp_max(valid ? fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)) : -inf);
-    const float W_ay0 = warp_min(valid ? fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)) : inf);
-    const float W_ay1 = warp_max(valid ? fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)) : -inf);
-    const float W_e = warp_max(valid ? emax : 0.0f);
-    const float W_l = warp_max(valid ? lmax : 0.0f);
-    const bool W_any = __any_sync(0xffffffffu, valid);
+    {
+      const float inf = __int_as_float(0x7f800000);
+      StripBox box;
+      box.tx0 = warp_min(valid ? xl : inf);
+      box.tx1 = warp_max(valid ? xr : -inf);
+      box.ty0 = warp_min(valid ? yb : inf);
+      box.ty1 = warp_max(valid ? yt : -inf);
+      box.ax0 = warp_min(valid ? fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)) : inf);
+      box.ax1 = warp_max(valid ? fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)) : -inf);
+      box.ay0 = warp_min(valid ? fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)) : inf);
+      box.ay1 = warp_max(valid ? fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)) : -inf);
+      box.e = warp_max(valid ? emax : 0.0f);
+      box.l = warp_max(valid ? lmax : 0.0f);
+      box.any = __any_sync(0xffffffffu, valid) ? 1 : 0;
+      box.pad = 0;
+      if (lane == 0) sb[wid] = box;
+    }
     const double* sxy = src.xy + (int64_t)sample * src.n_src * 2;
     const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
     for (int s0 = 0; s0 < src.n_src; s0 += kMaxSrcSmem) {
       const int sn = min(kMaxSrcSmem, src.n_src - s0);
       __syncthreads();
       for (int v = threadIdx.x; v < sn; v += kSearchThreads) {
-        float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
+        const float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
         ss[v] = SrcSmem{px, py, (float)sr[s0 + v],
                         u * (4.0f * g.theta_max + fabsf(px) + fabsf(py))};
       }
+      if (threadIdx.x < kStrips) n_surv[threadIdx.x] = 0;
       __syncthreads();
-      for (int k = 0; k < sn; ++k) {
+      // (1) one thread per (strip, source) pair
+      for (int pidx = threadIdx.x; pidx < kStrips * sn; pidx += kSearchThreads) {
+        const int w = pidx % kStrips, k = pidx / kStrips;
+        const StripBox B = sb[w];
         const SrcSmem S = ss[k];
-        {
-          // warp-uniform rejection of the whole strip (interval bound widened
-          // by the strip's largest vertex uncertainty and a relative margin)
-          const float wmu = fmaf(S.r, W_e, S.mu0 + u * (2.0f * (fabsf(W_tx0) + fabsf(W_tx1) +
-                                                                fabsf(W_ty0) + fabsf(W_ty1) +
-                                                                fabsf(S.px) + fabsf(S.py)) +
-                                                         4.0f * S.r * W_l));
-          const float bx0 = fmaf(-S.r, W_ax1, W_tx0), bx1 = fmaf(-S.r, W_ax0, W_tx1);
-          const float by0 = fmaf(-S.r, W_ay1, W_ty0), by1 = fmaf(-S.r, W_ay0, W_ty1);
-          if (!W_any || S.px < bx0 - wmu || S.px > bx1 + wmu || S.py < by0 - wmu ||
-              S.py > by1 + wmu)
-            continue;
-        }
+        const float wmu = fmaf(S.r, B.e, S.mu0 + u * (2.0f * (fabsf(B.tx0) + fabsf(B.tx1) +
+                                                              fabsf(B.ty0) + fabsf(B.ty1) +
+                                                              fabsf(S.px) + fabsf(S.py)) +
+                                                       4.0f * S.r * B.l));
+        const float bx0 = fmaf(-S.r, B.ax1, B.tx0), bx1 = fmaf(-S.r, B.ax0, B.tx1);
+        const float by0 = fmaf(-S.r, B.ay1, B.ty0), by1 = fmaf(-S.r, B.ay0, B.ty1);
+        const bool keep = B.any && S.px >= bx0 - wmu && S.px <= bx1 + wmu &&
+                          S.py >= by0 - wmu && S.py <= by1 + wmu;
+        if (keep) surv[w][atomicAdd(&n_surv[w], 1)] = (unsigned short)k;
+      }
+      __syncthreads();
+      // (2) each warp: its strip's surviving sources, one per iteration
+      const int ns = n_surv[wid];
+      for (int q = 0; q < ns; ++q) {
+        const int k = surv[wid][q];
+        const SrcSmem S = ss[k];
         const float dl = xl - S.px, dr = xr - S.px, db = yb - S.py, dt = yt - S.py;
         // relative mapped vertices beta_v - P = (theta_v - P) - r alpha_v
         const float a00x = fmaf(-S.r, v00.x, dl), a00y = fmaf(-S.r, v00.y, db);
@@ -320,7 +371,7 @@ __global__ void __launch_bounds__(kSearchThreads)
         const float maxx = fmaxf(fmaxf(a00x, a10x), fmaxf(a01x, a11x));
         const float miny = fminf(fminf(a00y, a10y), fminf(a01y, a11y));
         const float maxy = fmaxf(fmaxf(a00y, a10y), fmaxf(a01y, a11y));
-        bool cand = valid && minx <= mu && maxx >= -mu && miny <= mu && maxy >= -mu;
+        const bool cand = valid && minx <= mu && maxx >= -mu && miny <= mu && maxy >= -mu;
         int r0 = 0, r1 = 0;
         float w0[3], w1[3], pe0 = 0.0f, pe1 = 0.0f;
         if (cand) {
@@ -336,7 +387,6 @@ __global__ void __launch_bounds__(kSearchThreads)
           r0 = classify32(a00x, a00y, a10x, a10y, a11x, a11y, m00, m10, m11, w0, &pe0);
           r1 = classify32(a00x, a00y, a11x, a11y, a01x, a01y, m00, m11, m01, w1, &pe1);
         }
-        const float hmax = fmaxf((float)fabs(g.dx), (float)fabs(g.dy));
         const bool ok0 = r0 == 1 && pe0 * hmax <= (float)LT_POS_TOL;
         const bool ok1 = r1 == 1 && pe1 * hmax <= (float)LT_POS_TOL;
         const bool wk0 = r0 == 2 || (r0 == 1 && !ok0);
@@ -373,13 +423,13 @@ __global__ void __launch_bounds__(kSearchThreads)
       }
     }
   }
-  // block-level counter update (one atomic per counter per block)
+  // block-level counter update (one atomic per counter per warp)
   for (int o = 16; o > 0; o >>= 1) {
     n_hit += __shfl_xor_sync(0xffffffffu, n_hit, o);
     n_amb += __shfl_xor_sync(0xffffffffu, n_amb, o);
     n_ref += __shfl_xor_sync(0xffffffffu, n_ref, o);
   }
-  if ((threadIdx.x & 31) == 0 && (n_hit | n_amb | n_ref)) {
+  if (lane == 0 && (n_hit | n_amb | n_ref)) {
     atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
     atomicAdd((unsigned long long*)&counters[CNT_AMBIG], (unsigned long long)n_amb);
     atomicAdd((unsigned long long*)&counters[CNT_REFINE], (unsigned long long)n_ref);
@@ -390,8 +440,8 @@ cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const 
                             int n_samples, int64_t n_items, Sources src, Hit* hits,
                             int64_t hit_cap, Work64* work, int64_t work_cap,
                             unsigned long long* hit_count, unsigned long long* work_count,
-                            long long* counters, uint32_t* status, int sm_count,
-                            cudaStream_t st) {
+                            long long* counters, uint32_t* status,
+                            unsigned long long* next_item, int sm_count, cudaStream_t st) {
   if (n_items <= 0 || src.n_src <= 0) return cudaSuccess;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search32, kSearchThreads, 0);
@@ -401,7 +451,7 @@ cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const 
   k_search32<<<(unsigned)blocks, kSearchThreads, 0, st>>>(nodes, grids, item_off, n_samples,
                                                           n_items, src, hits, hit_cap, work,
                                                           work_cap, hit_count, work_count,
-                                                          counters, status);
+                                                          counters, status, next_item);
   return cudaGetLastError();
 }
 

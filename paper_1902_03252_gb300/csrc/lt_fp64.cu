@@ -347,27 +347,25 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
   return cudaGetLastError();
 }
 
-constexpr int kWarpsPerBlock64 = 4;
 
-__global__ void __launch_bounds__(32 * kWarpsPerBlock64)
+constexpr int kResolveThreads = 128;
+
+// One block per work item (items strided over blocks): the three vertex
+// deflections of the item's triangle in FP64 by the whole block, then the
+// exact predicate and interpolation by thread 0.
+__global__ void __launch_bounds__(kResolveThreads)
     k_resolve64(const Pot64* __restrict__ pot64, int n_pot, const SampleGrid* __restrict__ grids,
                 Sources src, const Work64* __restrict__ work,
                 const unsigned long long* __restrict__ work_count, int n_samples, int64_t work_cap,
                 Hit* __restrict__ hits, int64_t hit_cap, unsigned long long* hit_count,
                 long long* counters, uint32_t* status) {
-  __shared__ double2 buf[kWarpsPerBlock64][3 * 32];
-  __shared__ double res[kWarpsPerBlock64][6];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock64 + wid;
-  const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock64;
+  __shared__ double2 buf[3 * kResolveThreads];
+  __shared__ double res[6];
   long long n_nodes = 0, n_hit = 0;
-  for (int64_t f = gw; f < (int64_t)n_samples * work_cap; f += nw) {
+  for (int64_t f = blockIdx.x; f < (int64_t)n_samples * work_cap; f += gridDim.x) {
     const int b = (int)(f / work_cap);
     const int64_t idx = f - (int64_t)b * work_cap;
-    unsigned long long cnt = work_count[b];
-    if ((unsigned long long)idx >= cnt) {  // skip the rest of this sample quickly
-      continue;
-    }
+    if ((unsigned long long)idx >= work_count[b]) continue;  // block-uniform
     const Work64 wk = work[f];
     const SampleGrid g = grids[b];
     const int64_t cell = wk.tri / 2;
@@ -381,23 +379,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock64)
       X[v] = g.x0 + (double)(i + di[v]) * g.dx;
       Y[v] = g.y0 + (double)(j + dj[v]) * g.dy;
     }
-    warp_alpha64(pot64 + (int64_t)wk.sample * n_pot, n_pot, 3, X, Y, &res[wid][0], &res[wid][3],
-                 buf[wid]);
+    block_alpha64<kResolveThreads>(pot64 + (int64_t)wk.sample * n_pot, n_pot, 3, X, Y, &res[0],
+                                   &res[3], buf);
     n_nodes += 3;
-    bool in = false;
-    Hit h;
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
       const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
       const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
       const double Px = sxy[2 * wk.src], Py = sxy[2 * wk.src + 1];
       double Bx[3], By[3];
       for (int v = 0; v < 3; ++v) {
-        Bx[v] = X[v] - r * res[wid][v];
-        By[v] = Y[v] - r * res[wid][3 + v];
+        Bx[v] = X[v] - r * res[v];
+        By[v] = Y[v] - r * res[3 + v];
       }
       double w[3];
-      in = in_tri64(Bx[0], By[0], Bx[1], By[1], Bx[2], By[2], Px, Py, w);
-      if (in) {
+      if (in_tri64(Bx[0], By[0], Bx[1], By[1], Bx[2], By[2], Px, Py, w)) {
+        Hit h;
         h.src = wk.src;
         h.fp64 = 1;
         h.tri = wk.tri;
@@ -408,9 +404,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock64)
         ++n_hit;
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
-  if (lane == 0 && (n_nodes || n_hit)) {
+  if (threadIdx.x == 0 && (n_nodes || n_hit)) {
     atomicAdd((unsigned long long*)&counters[CNT_FP64_NODES], (unsigned long long)n_nodes);
     atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
   }
@@ -422,7 +418,7 @@ cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* gr
                              unsigned long long* hit_count, long long* counters,
                              uint32_t* status, int sm_count, cudaStream_t st) {
   int blocks = sm_count * 8;
-  k_resolve64<<<blocks, 32 * kWarpsPerBlock64, 0, st>>>(pot64, n_pot, grids, src, work,
+  k_resolve64<<<blocks, kResolveThreads, 0, st>>>(pot64, n_pot, grids, src, work,
                                                         work_count, n_samples, work_cap, hits,
                                                         hit_cap, hit_count, counters, status);
   return cudaGetLastError();
@@ -431,26 +427,25 @@ cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* gr
 // -------------------------------------------------------------- barycentres
 // beta_m = theta_obs,m - r_i alpha(theta_obs,m) for every (sample, observed
 // image); then each system's unweighted mean in observation order.
-__global__ void __launch_bounds__(32 * kWarpsPerBlock64)
+constexpr int kBaryThreads = 128;
+
+__global__ void __launch_bounds__(kBaryThreads)
     k_bary_obs(const Pot64* __restrict__ pot64, int n_pot, int batch, lt_obs obs,
                double* __restrict__ beta_obs) {
-  __shared__ double2 buf[kWarpsPerBlock64][3 * 32];
-  __shared__ double res[kWarpsPerBlock64][6];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock64 + wid;
-  const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock64;
-  for (int64_t f = gw; f < (int64_t)batch * obs.n_obs; f += nw) {
+  __shared__ double2 buf[3 * kBaryThreads];
+  __shared__ double res[6];
+  for (int64_t f = blockIdx.x; f < (int64_t)batch * obs.n_obs; f += gridDim.x) {
     const int b = (int)(f / obs.n_obs);
     const int m = (int)(f - (int64_t)b * obs.n_obs);
     double X = obs.x[m], Y = obs.y[m];
-    warp_alpha64(pot64 + (int64_t)b * n_pot, n_pot, 1, &X, &Y, &res[wid][0], &res[wid][3],
-                 buf[wid]);
-    if (lane == 0) {
+    block_alpha64<kBaryThreads>(pot64 + (int64_t)b * n_pot, n_pot, 1, &X, &Y, &res[0], &res[3],
+                                buf);
+    if (threadIdx.x == 0) {
       const double r = obs.dls_ds[obs.sys[m]];
-      beta_obs[2 * f] = X - r * res[wid][0];
-      beta_obs[2 * f + 1] = Y - r * res[wid][3];
+      beta_obs[2 * f] = X - r * res[0];
+      beta_obs[2 * f + 1] = Y - r * res[3];
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -474,11 +469,9 @@ __global__ void k_bary_sys(int batch, lt_obs obs, const double* __restrict__ bet
 
 cudaError_t launch_barycentres(const Pot64* pot64, int n_pot, int batch, const lt_obs& obs,
                                double* beta_obs, double* bary, cudaStream_t st) {
-  int64_t warps = (int64_t)batch * obs.n_obs;
-  int64_t blocks = (warps + kWarpsPerBlock64 - 1) / kWarpsPerBlock64;
-  if (blocks > 4096) blocks = 4096;
-  k_bary_obs<<<(unsigned)blocks, 32 * kWarpsPerBlock64, 0, st>>>(pot64, n_pot, batch, obs,
-                                                                 beta_obs);
+  int64_t blocks = (int64_t)batch * obs.n_obs;
+  if (blocks > 8192) blocks = 8192;
+  k_bary_obs<<<(unsigned)blocks, kBaryThreads, 0, st>>>(pot64, n_pot, batch, obs, beta_obs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t n = (int64_t)batch * obs.n_sys;

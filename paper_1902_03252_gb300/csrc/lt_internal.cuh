@@ -43,8 +43,9 @@ static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 //           f[2] = {a, s, q2*a, q2*s}; f[3] = {s-a, q2(s+a)(s-a), q2(s-a), B}
 //   all   : f[4] = {errP0, errGx, errGy, errQ} (error-bound coefficients; SIS
 //           and SIE use errP0 only, errQ is summed into Seg32::q_tot)
-// errP0 * (4 Theta + |cx| + |cy|) is the translation-error coefficient of the
-// running bound (Theta = largest |node coordinate| of the grid).
+// errP0 * (Theta + |cx| + |cy|) is the translation-error coefficient of the
+// running bound (Theta = largest |node coordinate| of the grid; node
+// coordinates are rounded once from FP64).
 struct Pot32 {
   float4 f[5];
 };
@@ -127,41 +128,45 @@ __device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, 
 }
 
 // ------------------------------------------------- FP64 point deflections
-// Deflection at up to 3 points by one warp: lanes evaluate potentials of a
-// 32-potential chunk in parallel into shared memory, then lane p sums point
-// p's contributions sequentially in potential index order.
-__device__ inline void warp_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts, const double* px,
-                             const double* py, double* ax, double* ay, double2* buf /*[3][32]*/) {
-  const int lane = threadIdx.x & 31;
+// Deflection at up to 3 points by a whole block of NT threads: thread t evaluates (point q,
+// potential c0 + t) for every point of a chunk of NT potentials, then thread
+// q sums point q's chunk in index order.  GB300's FP64 unit issues a warp
+// instruction only every few dozen cycles per SM sub-partition, so spreading
+// one evaluation over all four sub-partitions of an SM matters.  Must be
+// called by every thread of the block; results in ax[q], ay[q] (shared).
+template <int NT>
+__device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts,
+                                     const double* px, const double* py, double* ax, double* ay,
+                                     double2* buf /*[3][NT]*/) {
+  const int t = threadIdx.x;
   double sx = 0.0, sy = 0.0;
-  for (int c0 = 0; c0 < n_pot; c0 += 32) {
-    const int k = c0 + lane;
+  for (int c0 = 0; c0 < n_pot; c0 += NT) {
+    const int k = c0 + t;
     if (k < n_pot) {
       const Pot64 p = pb[k];
       for (int q = 0; q < npts; ++q) {
         double kx, ky;
         alpha64_one(p, px[q], py[q], kx, ky);
-        buf[q * 32 + lane] = make_double2(kx, ky);
+        buf[q * NT + t] = make_double2(kx, ky);
       }
     }
-    __syncwarp();
-    if (lane < npts) {
-      const int cn = min(32, n_pot - c0);
+    __syncthreads();
+    if (t < npts) {
+      const int cn = min(NT, n_pot - c0);
       for (int m = 0; m < cn; ++m) {
-        double2 v = buf[lane * 32 + m];
+        const double2 v = buf[t * NT + m];
         sx = sx + v.x;
         sy = sy + v.y;
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
-  if (lane < npts) {
-    ax[lane] = sx;
-    ay[lane] = sy;
+  if (t < npts) {
+    ax[t] = sx;
+    ay[t] = sy;
   }
-  __syncwarp();
+  __syncthreads();
 }
-
 
 // ---------------------------------------------------- FP32 special functions
 // atan(t)/t of t2 = t*t >= 0, branch-free: for t2 <= 1 a degree-8 polynomial
@@ -249,10 +254,11 @@ struct Hit {
 // All launchers enqueue on `st` and return the cudaGetLastError() value.
 cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,
                         Seg32* seg, uint32_t* status, cudaStream_t st);
+// next_item: a zeroed device counter, taken by atomicAdd (dynamic items)
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
                              const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, float4* node_out, int sm_count,
-                             cudaStream_t st);
+                             int64_t n_items, int shape, float4* node_out,
+                             unsigned long long* next_item, int sm_count, cudaStream_t st);
 cudaError_t launch_deflect64(const Pot64* pot64, int n_pot, const SampleGrid* grids,
                              const int64_t* item_off, int n_samples, int64_t n_items,
                              double2* node_out, int sm_count, cudaStream_t st);
@@ -273,8 +279,8 @@ cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const 
                             int n_samples, int64_t n_items, Sources src, Hit* hits,
                             int64_t hit_cap, Work64* work, int64_t work_cap,
                             unsigned long long* hit_count, unsigned long long* work_count,
-                            long long* counters, uint32_t* status, int sm_count,
-                            cudaStream_t st);
+                            long long* counters, uint32_t* status,
+                            unsigned long long* next_item, int sm_count, cudaStream_t st);
 cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const int64_t* item_off,
                             int n_samples, int64_t n_items, Sources src, Hit* hits,
                             int64_t hit_cap, unsigned long long* hit_count, long long* counters,

@@ -69,8 +69,7 @@ __global__ void __launch_bounds__(kNT)
   __shared__ float4 sp[256 * 5];
   const Seg32 sg = *seg;
   const int64_t nodes = (int64_t)g.nx * g.ny;
-  const float x0 = (float)g.x0, y0 = (float)g.y0, hx = (float)g.dx, hy = (float)g.dy;
-  const float theta4 = 4.0f * g.theta_max;
+  const float theta1 = g.theta_max;
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int64_t base = item * (int64_t)(kNT * kNPT);
     float X[kNPT], Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
@@ -80,8 +79,10 @@ __global__ void __launch_bounds__(kNT)
       if (n >= nodes) n = nodes - 1;
       const int j = (int)(n / g.nx);
       const int i = (int)(n - (int64_t)j * g.nx);
-      X[m] = fmaf((float)i, hx, x0);
-      Y[m] = fmaf((float)j, hy, y0);
+      // node coordinates rounded once from FP64: error u|theta| (App. A's
+      // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
+      X[m] = (float)(g.x0 + (double)i * g.dx);
+      Y[m] = (float)(g.y0 + (double)j * g.dy);
       AX[m] = 0.0f;
       AY[m] = 0.0f;
       ER[m] = 0.0f;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kNT)
         float4 val = pot32[c0 + k].f[w];
         if (w == 4) {
           const float4 h = pot32[c0 + k].f[0];
-          val.x = val.x * (theta4 + fabsf(h.x) + fabsf(h.y));
+          val.x = val.x * (theta1 + fabsf(h.x) + fabsf(h.y));
         }
         sp[v] = val;
       }
