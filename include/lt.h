@@ -8,11 +8,11 @@
  *   - sums the scaled deflection of all potentials at every node of an
  *     image-plane grid (Sect. 2.2.2, Algorithm 1 and its superposition),
  *   - maps nodes to the source plane, beta = theta - (D_ls/D_s) alpha
- *     (Eq. 11),
+ *     (Eq. 13),
  *   - splits every cell into two triangles and tests each mapped triangle
  *     for containing each source / system barycentre (Sect. 2.2.2, Fig. 1),
  *   - interpolates predicted image positions by barycentric weights,
- *   - reduces chi^2 = sum_ij |x_obs,ij - x_ij|^2 / sigma_ij^2 (Eq. 8),
+ *   - reduces chi^2 = sum_ij |x_obs,ij - x_ij|^2 / sigma_ij^2 (Eq. 11),
  *   - and differentiates chi^2 w.r.t. the lens parameters with the triangle
  *     assignment held fixed.
  *
@@ -61,7 +61,23 @@ typedef enum { LT_SIS = 0, LT_PIEMD = 1, LT_SIE = 2 } lt_kind;
  * orientation signs are not certain under that bound, and a hit whose FP32
  * position bound exceeds LT_POS_TOL, are re-evaluated in FP64 with the three
  * vertex deflections recomputed in FP64.  Image sets equal the FP64 ones. */
-typedef enum { LT_PREC_FP64 = 0, LT_PREC_MIXED = 1 } lt_precision;
+typedef enum { LT_PREC_FP64 = 0, LT_PREC_MIXED = 1, LT_PREC_PAPER = 2 } lt_precision;
+
+/* LT_PREC_PAPER (lt_deflect_grid only): the paper's own mixed-precision rule
+ * for the deflection grid (Sect. 3.3 and App. A.3).  Every node is computed
+ * in FP32; then every node is recomputed in FP64 that lies
+ *   - in a square patch centred on a halo: 400 x 400 nodes around
+ *     cluster-scale halos (b0 >= LT_PAPER_CLUSTER_B0 arcsec), 20 x 20 around
+ *     the others (galaxy scale), or
+ *   - where the distortion criteria fire on the FP32 grid (Eqs. 23-28):
+ *     |h - d1| or |h - d2| < 0.0092 h/0.03, or |d3| or |d4| > 0.0104 h/0.03,
+ *     with d1 = a1(i,j) - a1(i-1,j), d2 = a2(i,j) - a2(i,j-1),
+ *     d3 = a1(i,j) - a1(i,j-1), d4 = a2(i,j) - a2(i-1,j), h the node spacing
+ *     (the paper's thresholds for 0.03" pixels, scaled with the spacing;
+ *     nodes in the first row or column have no criteria).
+ * alpha_out is then double [ny][nx][2]; err_out (optional) receives 1.0 at
+ * the nodes recomputed in FP64 and 0.0 elsewhere. */
+#define LT_PAPER_CLUSTER_B0 1.0
 
 /* Position tolerance (arcsec) that an FP32 interpolated image must provably
  * meet; otherwise the hit is re-interpolated in FP64. */
@@ -151,9 +167,10 @@ lt_status lt_model_set_params(lt_model* model, const double* params, int on_devi
 /* Deflection field of one sample over one grid (Sect. 2.2.2: the gradient of
  * the lensing potential summed over all potentials at every node).
  * alpha_out: device, [ny][nx][2] of float (LT_PREC_MIXED) or double
- * (LT_PREC_FP64).  err_out: optional device [ny][nx] float receiving the FP32
- * running error bound of each node (LT_PREC_MIXED only; pass NULL
- * otherwise).  Errors: LT_ERR_INVALID_ARG. */
+ * (LT_PREC_FP64, LT_PREC_PAPER).  err_out: optional device [ny][nx] float
+ * receiving the FP32 running error bound of each node (LT_PREC_MIXED) or the
+ * FP64-recomputation map (LT_PREC_PAPER); NULL with LT_PREC_FP64.
+ * Errors: LT_ERR_INVALID_ARG. */
 lt_status lt_deflect_grid(lt_model* model, int32_t sample, const lt_grid* grid,
                           lt_precision precision, void* alpha_out, float* err_out,
                           uintptr_t stream);
@@ -169,7 +186,7 @@ lt_status lt_find_images(lt_model* model, const lt_grid* grids, int32_t n_src,
                          const double* src_xy, const double* dls_ds, lt_precision precision,
                          int64_t capacity, lt_image* out, int64_t* n_out, uintptr_t stream);
 
-/* chi^2 of Eq. 8 for every sample: observed images mapped to the source
+/* chi^2 of Eq. 11 for every sample: observed images mapped to the source
  * plane, per-system barycentres (FP64), triangle search for each barycentre,
  * barycentric image positions, and for each observed image the nearest
  * predicted image of its system (ties to the lower triangle id); a system
@@ -252,6 +269,17 @@ lt_status lt_profile_read(lt_model* model, lt_profile* out, int reset);
 lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot, const lt_grid* grid,
                                   float* alpha_out, float* err_out, int32_t* status_out,
                                   uintptr_t stream);
+
+/* D_ls/D_s of a source at redshift z_s behind a lens at z_l (Sect. 4: the
+ * paper's benchmark puts the lens at 0.3 and the sources at 2.0 in flat
+ * LambdaCDM, Omega_m = 0.3, Omega_Lambda = 0.7), the ratio that scales the
+ * deflection in the lens equation (Eq. 13).  Host computation: angular
+ * diameter distances from the comoving distance integral (Gauss-Legendre
+ * quadrature); H0 cancels.  Requires 0 <= z_l < z_s, Omega_m >= 0 and
+ * Omega_k = 1 - Omega_m - Omega_Lambda >= 0 (flat or open); otherwise
+ * LT_ERR_INVALID_ARG.  No model or GPU is needed. */
+lt_status lt_dls_ds(double z_l, double z_s, double omega_m, double omega_lambda,
+                    double* dls_ds);
 
 /* Library version string. */
 const char* lt_version(void);

@@ -163,7 +163,7 @@ def barycentres(params, obs):
 
 
 def chi2(params, grid, obs, n_threads: int = 1, capacity: int = 1 << 16):
-    """Full chi^2 of Eq. 8 for one sample; returns a dict of all intermediates."""
+    """Full chi^2 of Eq. 11 for one sample; returns a dict of all intermediates."""
     x0, y0, dx, dy, nx, ny = grid
     p, pp = _d(_params(params))
     ox, oxp = _d(obs["x"])
@@ -221,3 +221,22 @@ def chi2_grad(params, grid, obs, match_tri):
     lib().lto_chi2_grad(pp, p.shape[1], x0, y0, dx, dy, nx, ny, ox.size, oxp, oyp, sgp, osp,
                         r.size, rp, mtp, C.byref(c2), gp)
     return c2.value, g
+
+
+def dls_ds(z_l, z_s, omega_m=0.3, omega_lambda=0.7):
+    """D_ls/D_s by adaptive quadrature of the comoving distance (scipy), for
+    flat or open cosmologies: D_M12 / D_M2 with D_M the transverse comoving
+    distance and D_M12 = D_M2 sqrt(1 + Ok D_M1^2) - D_M1 sqrt(1 + Ok D_M2^2)."""
+    from scipy import integrate
+    ok = 1.0 - omega_m - omega_lambda
+
+    def dc(z):
+        f = lambda x: 1.0 / np.sqrt(omega_m * (1 + x) ** 3 + ok * (1 + x) ** 2 + omega_lambda)
+        return integrate.quad(f, 0.0, z, epsabs=0, epsrel=1e-13, limit=200)[0]
+
+    def dm(z):
+        d = dc(z)
+        return np.sinh(np.sqrt(ok) * d) / np.sqrt(ok) if ok > 1e-12 else d
+    m1, m2 = dm(z_l), dm(z_s)
+    okc = max(ok, 0.0)
+    return (m2 * np.sqrt(1 + okc * m1 * m1) - m1 * np.sqrt(1 + okc * m2 * m2)) / m2

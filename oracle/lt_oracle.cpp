@@ -15,13 +15,13 @@
  *   1. alpha(theta) = sum over potentials of the per-potential scaled
  *      deflection, in potential index order (superposition of gradients,
  *      Sect. 2.2.2; Algorithm 1 for the SIE).
- *   2. beta = theta - (D_ls/D_s) alpha(theta)   (lens equation, Eq. 11).
+ *   2. beta = theta - (D_ls/D_s) alpha(theta)   (lens equation, Eq. 13).
  *   3. barycentre of each system: mean over its observed images of beta.
  *   4. every grid cell split into two triangles; every mapped triangle
  *      tested for containing each system's barycentre (Fig. 1).
  *   5. predicted image = barycentric interpolation inside a containing
  *      triangle.
- *   6. chi^2 = sum_i sum_j |x_obs,ij - x_ij|^2 / sigma_ij^2  (Eq. 8), each
+ *   6. chi^2 = sum_i sum_j |x_obs,ij - x_ij|^2 / sigma_ij^2  (Eq. 11), each
  *      observed image matched to the nearest predicted image of its system.
  *   7. d chi^2 / d(params) with the triangle assignment and matching frozen,
  *      by forward-mode dual numbers through the same templated code.
@@ -95,7 +95,7 @@ using std::sqrt;
 
 // ------------------------------------------------------------ per-potential
 // b0 = 4 pi (sigma_v / c)^2, the SIS/SIE normalisation of Sect. 2.2.2
-// (the scaled deflection with D_ls/D_s factored out, Eq. 10), in arcsec.
+// (the scaled deflection with D_ls/D_s factored out, Eq. 12), in arcsec.
 template <class T>
 T b0_of(T sv) {
   T t = sv / kC;
@@ -444,7 +444,7 @@ int lto_barycentres(const double* params, int n_pot, int n_obs, const double* ox
 }
 
 /*
- * chi^2 of Eq. 8 for one sample.  For each observed image (in observation
+ * chi^2 of Eq. 11 for one sample.  For each observed image (in observation
  * order) the predicted image of its system nearest to it is taken (ties to
  * the lower triangle id); a system with no predicted image contributes
  * (L_diag / sigma)^2 per observed image, L_diag the grid diagonal.

@@ -1,11 +1,11 @@
 // Hand-written adjoint of the chi^2 path with the triangle assignment and the
 // image matching of the forward evaluation held fixed.
 //
-// chi^2 = sum_m |x_obs,m - x_m|^2 / sigma_m^2 (Eq. 8) with
+// chi^2 = sum_m |x_obs,m - x_m|^2 / sigma_m^2 (Eq. 11) with
 //   x_m = theta_A + w_B (theta_B - theta_A) + w_C (theta_C - theta_A) inside the
 //   matched triangle, where (w_B, w_C) solve
 //   [beta_B - beta_A, beta_C - beta_A] (w_B, w_C)^T = beta_bar - beta_A,
-//   beta_v = theta_v - r alpha(theta_v) (Eq. 11) and beta_bar the system's
+//   beta_v = theta_v - r alpha(theta_v) (Eq. 13) and beta_bar the system's
 //   barycentre of theta_obs - r alpha(theta_obs).
 // With G = dchi^2/dx of a predicted image and lambda = M^-T (G.(theta_B -
 // theta_A), G.(theta_C - theta_A)), dchi^2 = lambda . (dbeta_bar - sum_v w_v

@@ -553,9 +553,11 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   LT_CHECK_ARG(sample >= 0 && sample < m->batch, "sample out of range");
   LT_CHECK_ARG(grid && grid_ok(*grid), "invalid grid");
   LT_CHECK_ARG(alpha_out != nullptr, "alpha_out is NULL");
-  LT_CHECK_ARG(precision == LT_PREC_FP64 || precision == LT_PREC_MIXED, "invalid precision");
-  LT_CHECK_ARG(precision == LT_PREC_MIXED || err_out == nullptr,
-               "err_out is only produced in mixed precision");
+  LT_CHECK_ARG(precision == LT_PREC_FP64 || precision == LT_PREC_MIXED ||
+                   precision == LT_PREC_PAPER,
+               "invalid precision");
+  LT_CHECK_ARG(precision != LT_PREC_FP64 || err_out == nullptr,
+               "err_out is not produced in FP64 precision");
   cudaStream_t st = S(stream);
   // a one-sample plan over the caller's grid (does not disturb the batch plan)
   const lt_grid& g = *grid;
@@ -567,43 +569,58 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   sg.theta_max = (float)(tm * (1.0 + 1e-6));
   sg.pad = 0.f;
   const int64_t nodes = (int64_t)g.nx * g.ny;
-  const int64_t dn = defl_item_nodes(precision, m->shape);
+  LT_CHECK_ARG(precision != LT_PREC_PAPER || nodes < ((int64_t)1 << 31),
+               "LT_PREC_PAPER grids are limited to 2^31 nodes");
+  const int64_t dn = defl_item_nodes(precision == LT_PREC_FP64 ? LT_PREC_FP64 : LT_PREC_MIXED,
+                                     m->shape);
   int64_t items[2] = {0, (nodes + dn - 1) / dn};
-  // a private device copy: [SampleGrid][2 x int64]
   static_assert(sizeof(SampleGrid) % 8 == 0, "alignment");
   struct OneSample {
     SampleGrid g;
     int64_t items[2];
-  } host{sg, {items[0], items[1]}};
-  // the sample's plan lives after its nodes in the node workspace, so the
-  // batch plan's tables stay intact
-  const size_t node_bytes = precision == LT_PREC_FP64 ? 0 : sizeof(float4) * (size_t)nodes;
-  lt_status s = ensure_nodes(m, node_bytes + sizeof(OneSample) + 256);
+    unsigned long long count;
+  } host{sg, {items[0], items[1]}, 0ull};
+  // node workspace layout: [float4 nodes][flags][int32 list][OneSample]; the
+  // sample's plan lives after its nodes, so the batch plan's tables stay intact
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t node_bytes = precision == LT_PREC_FP64 ? 0 : up(sizeof(float4) * (size_t)nodes);
+  const size_t flag_bytes = precision == LT_PREC_PAPER ? up((size_t)nodes) : 0;
+  const size_t list_bytes = precision == LT_PREC_PAPER ? up(sizeof(int32_t) * (size_t)nodes) : 0;
+  const size_t need = node_bytes + flag_bytes + list_bytes + up(sizeof(OneSample));
+  lt_status s = ensure_nodes(m, need);
   if (s != LT_OK) return s;
   char* base = (char*)m->d_nodes;
-  OneSample* dev = (OneSample*)(base + ((node_bytes + 255) / 256) * 256);
-  if ((char*)dev + sizeof(OneSample) > base + m->nodes_bytes) {
-    s = ensure_nodes(m, ((node_bytes + 255) / 256) * 256 + sizeof(OneSample));
-    if (s != LT_OK) return s;
-    base = (char*)m->d_nodes;
-    dev = (OneSample*)(base + ((node_bytes + 255) / 256) * 256);
-  }
+  unsigned char* flags = (unsigned char*)(base + node_bytes);
+  int32_t* list = (int32_t*)(base + node_bytes + flag_bytes);
+  OneSample* dev = (OneSample*)(base + node_bytes + flag_bytes + list_bytes);
   LT_CUDA(cudaMemcpyAsync(dev, &host, sizeof(OneSample), cudaMemcpyHostToDevice, st));
   if (precision == LT_PREC_FP64) {
     LT_CUDA(launch_deflect64(m->d_pot64 + (size_t)sample * m->n_pot, m->n_pot, &dev->g,
                              dev->items, 1, items[1], (double2*)alpha_out, m->sm_count, st));
-  } else {
-    float4* nodes4 = (float4*)base;
-    if (!m->d_sched) {
-      lt_status s2 = grow(m, &m->d_sched, &m->sched_alloc, 1);
-      if (s2 != LT_OK) return s2;
-    }
-    LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long), st));
-    LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)sample * m->n_pot, m->d_seg + sample, m->n_pot,
-                             &dev->g, dev->items, 1, items[1], m->shape, nodes4, m->d_sched,
-                             m->sm_count, st));
-    LT_CUDA(launch_unpack32(nodes4, nodes, (float2*)alpha_out, err_out, st));
+    return LT_OK;
   }
+  float4* nodes4 = (float4*)base;
+  if (!m->d_sched) {
+    lt_status s2 = grow(m, &m->d_sched, &m->sched_alloc, 1);
+    if (s2 != LT_OK) return s2;
+  }
+  LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long), st));
+  LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)sample * m->n_pot, m->d_seg + sample, m->n_pot,
+                           &dev->g, dev->items, 1, items[1], m->shape, nodes4, m->d_sched,
+                           m->sm_count, st));
+  if (precision == LT_PREC_MIXED) {
+    LT_CUDA(launch_unpack32(nodes4, nodes, (float2*)alpha_out, err_out, st));
+    return LT_OK;
+  }
+  // the paper's rule: FP32 widened, FP64 in halo patches and where the
+  // distortion criteria fire
+  const Pot64* p64 = m->d_pot64 + (size_t)sample * m->n_pot;
+  LT_CUDA(launch_paper_flags(nodes4, p64, m->n_pot, g, (double2*)alpha_out, flags, list,
+                             &dev->count, err_out, m->sm_count, st));
+  LT_CUDA(launch_paper_fp64(p64, m->n_pot, g, list, &dev->count, (double2*)alpha_out,
+                            m->sm_count, st));
+  LT_CUDA(cudaMemcpyAsync(&m->d_counters[CNT_FP64_NODES], &dev->count, sizeof(long long),
+                          cudaMemcpyDeviceToDevice, st));
   return LT_OK;
 }
 

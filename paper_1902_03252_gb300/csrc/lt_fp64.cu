@@ -6,12 +6,12 @@
 //                 rotations, axis ratios; FP64 records in index order and
 //                 FP32 records grouped by kind with error-bound coefficients.
 //   k_deflect64   FP64 deflection of every node (Sect. 2.2.2, Algorithm 1).
-//   k_search64    FP64 lens mapping (Eq. 11) and exact triangle predicate.
+//   k_search64    FP64 lens mapping (Eq. 13) and exact triangle predicate.
 //   k_resolve64   FP64 re-evaluation of the pairs the FP32 filter could not
 //                 certify and of FP32 hits whose position bound is too large.
 //   k_bary_obs / k_bary_sys   barycentres of the observed systems.
 //   k_sort_hits   images of each sample in (source, triangle) order.
-//   k_chi2        nearest-image matching and the chi^2 of Eq. 8.
+//   k_chi2        nearest-image matching and the chi^2 of Eq. 11.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kSearch64Threads)
     const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
     for (int k = 0; k < src.n_src; ++k) {
       const double Px = sxy[2 * k], Py = sxy[2 * k + 1], r = sr[k];
-      // mapped vertices beta = theta - r alpha (Eq. 11)
+      // mapped vertices beta = theta - r alpha (Eq. 13)
       const double b00x = X0 - r * a00.x, b00y = Y0 - r * a00.y;
       const double b10x = X1 - r * a10.x, b10y = Y0 - r * a10.y;
       const double b01x = X0 - r * a01.x, b01y = Y1 - r * a01.y;
@@ -599,6 +599,55 @@ cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, in
   if (n_samples <= 0) return cudaSuccess;
   k_chi2<<<n_samples, kChi2Threads, 0, st>>>(hits, hit_count, hit_cap, sample_base, grids, obs,
                                              chi2, match_tri, match_hit, match_xy);
+  return cudaGetLastError();
+}
+
+}  // namespace lt
+
+namespace lt {
+
+// FP64 recomputation of the listed nodes (the paper's mixed rule): one node
+// per thread, potentials staged in shared memory and summed in index order,
+// exactly as the FP64 deflection kernel does.
+__global__ void __launch_bounds__(kDefl64Threads)
+    k_paper_fp64(const Pot64* __restrict__ pot64, int n_pot, double x0, double y0, double dx,
+                 double dy, int nx, const int32_t* __restrict__ list,
+                 const unsigned long long* __restrict__ count, double2* __restrict__ out) {
+  __shared__ Pot64 sp[kChunk64];
+  const int64_t n_list = (int64_t)*count;
+  for (int64_t base = (int64_t)blockIdx.x * kDefl64Threads; base < n_list;
+       base += (int64_t)gridDim.x * kDefl64Threads) {
+    const int64_t idx = base + threadIdx.x;
+    const bool valid = idx < n_list;
+    const int64_t n = valid ? list[idx] : list[base];
+    const int j = (int)(n / nx), i = (int)(n - (int64_t)j * nx);
+    const double x = x0 + (double)i * dx;
+    const double y = y0 + (double)j * dy;
+    double ax = 0.0, ay = 0.0;
+    for (int c0 = 0; c0 < n_pot; c0 += kChunk64) {
+      const int cn = min(kChunk64, n_pot - c0);
+      __syncthreads();
+      for (int k = threadIdx.x; k < cn; k += kDefl64Threads) sp[k] = pot64[c0 + k];
+      __syncthreads();
+      for (int k = 0; k < cn; ++k) {
+        double kx, ky;
+        alpha64_one(sp[k], x, y, kx, ky);
+        ax = ax + kx;
+        ay = ay + ky;
+      }
+    }
+    if (valid) out[n] = make_double2(ax, ay);
+  }
+}
+
+cudaError_t launch_paper_fp64(const Pot64* pot64, int n_pot, const lt_grid& g, const int32_t* list,
+                              const unsigned long long* count, double2* out, int sm_count,
+                              cudaStream_t st) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paper_fp64, kDefl64Threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  k_paper_fp64<<<sm_count * per_sm, kDefl64Threads, 0, st>>>(pot64, n_pot, g.x0, g.y0, g.dx, g.dy,
+                                                             g.nx, list, count, out);
   return cudaGetLastError();
 }
 

@@ -169,16 +169,26 @@ __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, in
 }
 
 // ---------------------------------------------------- FP32 special functions
-// atan(t)/t of t2 = t*t >= 0, branch-free: for t2 <= 1 a degree-8 polynomial
-// in t2 (least-squares fit at Chebyshev nodes, relative error < 1e-7; the
+// atan(t)/t of t2 = t*t >= 0: for t2 <= 1 a degree-8 polynomial in t2
+// (least-squares fit at Chebyshev nodes, relative error < 1e-7; the
 // coefficients come from csrc/fit_poly.py); for t2 > 1, atan(t) = pi/2 -
-// atan(1/t) gives (pi/2)/t - P(1/t2)/t2.  One MUFU rsqrt.
+// atan(1/t) gives (pi/2)/t - P(1/t2)/t2 with one MUFU rsqrt.  The range test
+// is a real branch: the 32 nodes of a warp see one potential from nearly the
+// same direction, so it is almost always uniform.
+//
+// atanh(t)/t of t2 = t*t in [0, 1): for t2 <= 1/4 a degree-5 polynomial in
+// t2 (same fit, relative error < 1.1e-7); above, atanh(t) = ln((1+t)/(1-t))/2
+// with MUFU rsqrt, rcp and lg2 (the ratio is >= 3 there, where lg2 has a
+// 2-ulp relative error).
 __device__ __forceinline__ float atanc_sq32(float t2) {
-  const float r = rsqrtf(t2);  // 1/t (infinite at t2 = 0, then unused)
-  const float inv = r * r;     // 1/t2
-  const bool big = t2 > 1.0f;
-  const float u = big ? inv : t2;
-  float p = 2.781707901e-03f;
+  float p, inv = 0.f, r = 0.f;
+  float u = t2;
+  if (t2 > 1.0f) {
+    r = rsqrtf(t2);
+    inv = r * r;
+    u = inv;
+  }
+  p = 2.781707901e-03f;
   p = fmaf(p, u, -1.579383570e-02f);
   p = fmaf(p, u, 4.224103530e-02f);
   p = fmaf(p, u, -7.465778757e-02f);
@@ -187,24 +197,23 @@ __device__ __forceinline__ float atanc_sq32(float t2) {
   p = fmaf(p, u, 1.999201744e-01f);
   p = fmaf(p, u, -3.333304396e-01f);
   p = fmaf(p, u, 9.999999824e-01f);
-  return big ? fmaf(1.57079633f, r, -(p * inv)) : p;
+  if (t2 > 1.0f) p = fmaf(1.57079633f, r, -(p * inv));
+  return p;
 }
-// atanh(t)/t of t2 = t*t in [0, 1), branch-free: for t2 <= 1/4 a degree-5
-// polynomial in t2 (same fit, relative error < 1.1e-7); above,
-// atanh(t) = ln((1+t)/(1-t))/2 with MUFU rsqrt, rcp and lg2 (the ratio is
-// >= 3 there, where lg2 has a 2-ulp relative error).
 __device__ __forceinline__ float atanhc_sq32(float t2) {
-  t2 = fminf(t2, 0.99999988f);
+  if (t2 > 0.25f) {
+    t2 = fminf(t2, 0.99999988f);
+    const float r = rsqrtf(t2);
+    const float t = t2 * r;
+    return __log2f(__fdividef(1.0f + t, 1.0f - t)) * (0.5f * 0.693147181f) * r;
+  }
   float p = 1.832424287e-01f;
   p = fmaf(p, t2, 8.136755977e-02f);
   p = fmaf(p, t2, 1.469695817e-01f);
   p = fmaf(p, t2, 1.997503703e-01f);
   p = fmaf(p, t2, 3.333387857e-01f);
   p = fmaf(p, t2, 9.999999809e-01f);
-  const float r = rsqrtf(t2);  // 1/t
-  const float t = t2 * r;
-  const float l = __log2f(__fdividef(1.0f + t, 1.0f - t)) * (0.5f * 0.693147181f) * r;
-  return t2 > 0.25f ? l : p;
+  return p;
 }
 
 // Launch-shape variants of the FP32 deflection kernel (autotuned).
@@ -299,6 +308,14 @@ cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const Sampl
                            const Hit* hits, int64_t hit_cap, const lt_obs& obs,
                            const int32_t* match_hit, double2* lam, AdjPt* pts, double* grad,
                            int sm_count, cudaStream_t st);
+// The paper's mixed rule for a deflection grid (LT_PREC_PAPER).
+cudaError_t launch_paper_flags(const float4* nodes, const Pot64* pot64, int n_pot,
+                               const lt_grid& g, double2* out, unsigned char* flags,
+                               int32_t* list, unsigned long long* count, float* map,
+                               int sm_count, cudaStream_t st);
+cudaError_t launch_paper_fp64(const Pot64* pot64, int n_pot, const lt_grid& g, const int32_t* list,
+                              const unsigned long long* count, double2* out, int sm_count,
+                              cudaStream_t st);
 cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, int n_samples,
                         int64_t hit_cap, int sample_base, const SampleGrid* grids,
                         const lt_obs& obs, double* chi2, int64_t* match_tri, int32_t* match_hit,

@@ -18,14 +18,14 @@ from . import _build
 LT_OK, LT_ERR_INVALID_ARG, LT_ERR_CUDA, LT_ERR_NOMEM, LT_ERR_OVERFLOW, LT_ERR_TIMEOUT, \
     LT_ERR_NONFINITE = range(7)
 LT_SIS, LT_PIEMD, LT_SIE = 0, 1, 2
-FP64, MIXED = 0, 1
+FP64, MIXED, PAPER = 0, 1, 2
 N_ROWS, N_GRAD = 8, 6
 POS_TOL = 2.5e-5
 
 EXPORTED = ("lt_model_create", "lt_model_destroy", "lt_last_error", "lt_status_string",
             "lt_model_set_params", "lt_deflect_grid", "lt_find_images", "lt_chi2",
             "lt_chi2_grad", "lt_last_matches", "lt_model_sync", "lt_chi2_graph",
-            "lt_autotune", "lt_profile_enable", "lt_profile_read", "lt_version")
+            "lt_autotune", "lt_profile_enable", "lt_profile_read", "lt_dls_ds", "lt_version")
 
 
 class Grid(C.Structure):
@@ -112,13 +112,16 @@ def load(build_if_missing: bool = False):
     L.lt_autotune.argtypes = [vp, C.POINTER(Grid), up, C.POINTER(i32)]
     L.lt_profile_enable.argtypes = [vp, C.c_int]
     L.lt_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
+    L.lt_dls_ds.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double,
+                            C.POINTER(C.c_double)]
     for name in EXPORTED:
         f = getattr(L, name)
         if f.restype is C.c_int or name in ("lt_model_create", "lt_model_set_params",
                                             "lt_deflect_grid", "lt_find_images", "lt_chi2",
                                             "lt_chi2_graph", "lt_chi2_grad", "lt_last_matches",
                                             "lt_model_sync", "lt_autotune",
-                                            "lt_profile_enable", "lt_profile_read"):
+                                            "lt_profile_enable", "lt_profile_read",
+                                            "lt_dls_ds"):
             f.restype = st
     _lib = L
     return L
@@ -216,12 +219,13 @@ class Model:
                         "lt_model_set_params")
 
     def deflect_grid(self, grid, precision=MIXED, sample=0, with_error=False, stream=None):
-        """[ny][nx][2] deflection (float32 mixed / float64 FP64) as a CUDA tensor,
-        plus the per-node FP32 error bound when ``with_error``."""
+        """[ny][nx][2] deflection (float32 for MIXED, float64 for FP64 and PAPER)
+        as a CUDA tensor, plus the per-node FP32 error bound (MIXED) or the
+        FP64-recomputation map (PAPER) when ``with_error``."""
         torch = _torch()
         g = grids_array([grid])
         nx, ny = g[0].nx, g[0].ny
-        dt = torch.float64 if precision == FP64 else torch.float32
+        dt = torch.float32 if precision == MIXED else torch.float64
         a = torch.empty((ny, nx, 2), dtype=dt, device="cuda")
         e = torch.empty((ny, nx), dtype=torch.float32, device="cuda") if with_error else None
         self._check(self._lib.lt_deflect_grid(self.h, sample, g, precision, _ptr(a), _ptr(e),
@@ -296,6 +300,15 @@ class Model:
         self._check(self._lib.lt_autotune(self.h, grids_array([grid]), _stream(stream),
                                           C.byref(ch)), "lt_autotune")
         return ch.value
+
+
+def dls_ds(z_l: float, z_s: float, omega_m: float = 0.3, omega_lambda: float = 0.7) -> float:
+    """D_ls/D_s for a lens at z_l and a source at z_s (host computation)."""
+    out = C.c_double(0.0)
+    st = load().lt_dls_ds(z_l, z_s, omega_m, omega_lambda, C.byref(out))
+    if st != LT_OK:
+        raise LTError(st, "lt_dls_ds: invalid redshifts or cosmology")
+    return out.value
 
 
 def images_to_numpy(out, counts):

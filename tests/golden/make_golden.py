@@ -60,7 +60,7 @@ def make_c1():
     g = w.grids[0].as_tuple()
     H, U = oracle.find_images(w.params[0], g, [beta], [r])
     _dump("c1_sis.json", {
-        "citation": "Eq. 1 (lens equation) with |alpha| = theta_E for the SIS (Sect. 2.1, Eq. 7): "
+        "citation": "Eq. 1 (lens equation) with |alpha| = theta_E for the SIS (Sect. 2.1, Eq. 10): "
                     "images at beta_hat (|beta| +/- theta_E), the minus image only for |beta| < theta_E",
         "beta": list(beta), "theta_e": te, "dls_ds": r, "grid": list(g),
         "closed_form_images": [list(i) for i in ims],

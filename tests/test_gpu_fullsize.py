@@ -1,0 +1,156 @@
+"""Parity at the workloads' full sizes, in the configuration the benchmark runs.
+
+* c2 (100 PIEMD, 2000^2, 20 systems): the oracle's whole chi^2 evaluation
+  (matches, positions, chi^2) against both precisions.
+* c3 (1024 perturbed samples, grids 500^2..2000^2, one call): the full oracle
+  evaluation of three samples drawn from the batch.
+* c5 (1000 PIEMD, 4000^2, 100 systems; two samples): outputs the oracle checks
+  one by one -- barycentres, the FP64 containment and barycentric position of
+  every matched triangle, sampled node deflections within their bound -- and
+  sampled gradient components against central differences of the oracle's
+  frozen-assignment chi^2.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1902_03252_gb300 import lt, workloads as W  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lt.load(build_if_missing=True)
+
+
+def load_obs(cfg):
+    with open(os.path.join(GOLDEN, f"obs_{cfg}.json")) as f:
+        return json.load(f)
+
+
+def chi2_tol(o, ref_xy, tol):
+    res = np.hypot(np.asarray(o["x"]) - ref_xy[:, 0], np.asarray(o["y"]) - ref_xy[:, 1])
+    return np.sum((2 * res * tol * 1.5 + 2 * tol * tol) / np.asarray(o["sigma"]) ** 2)
+
+
+def run(w, o, grids, prec, grad=False, capacity=0):
+    m = lt.Model(w.n_pot, w.batch, hit_capacity=capacity)
+    m.set_params(w.params)
+    obs = lt.Observations.from_dict(o)
+    if grad:
+        c2, g = m.chi2_grad(grids, obs, precision=prec)
+    else:
+        c2, g = m.chi2(grids, obs, precision=prec), None
+    st, stats = m.sync()
+    assert st == lt.LT_OK, st
+    mt, mxy, bary = m.last_matches(len(o["x"]), len(o["dls_ds"]))
+    out = dict(chi2=c2.cpu().numpy(), mt=mt.cpu().numpy(), mxy=mxy.cpu().numpy(),
+               bary=bary.cpu().numpy(), stats=stats, grad=None if g is None else g.cpu().numpy())
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [(lt.MIXED, 1e-4), (lt.FP64, 1e-9)])
+def test_c2_full_chi2(oracle, prec, tol):
+    w = W.c2()
+    o = load_obs("c2")
+    grid = w.grids[0].as_tuple()
+    r = run(w, o, [grid], prec)
+    ref = oracle.chi2(w.params[0], grid, o, n_threads=THREADS)
+    assert ref["n_undecidable"] == 0
+    assert np.array_equal(r["mt"][0], ref["match_tri"])
+    ok = ref["match_tri"] >= 0
+    assert np.abs(r["mxy"][0][ok] - ref["match_xy"][ok]).max() <= tol
+    np.testing.assert_allclose(r["bary"][0], ref["bary"], rtol=0, atol=1e-10)
+    assert abs(r["chi2"][0] - ref["chi2"]) <= chi2_tol(o, ref["match_xy"], tol) + 1e-12 * ref["chi2"]
+
+
+def test_c3_full_batch_sampled(oracle):
+    w = W.c3()
+    o = load_obs("c3")
+    grids = [g.as_tuple() for g in w.grids]
+    r = run(w, o, grids, lt.MIXED)
+    rng = np.random.default_rng(33)
+    for b in rng.choice(w.batch, 3, replace=False):
+        ref = oracle.chi2(w.params[b], grids[b], o, n_threads=THREADS)
+        assert ref["n_undecidable"] == 0
+        assert np.array_equal(r["mt"][b], ref["match_tri"]), b
+        ok = ref["match_tri"] >= 0
+        assert np.abs(r["mxy"][b][ok] - ref["match_xy"][ok]).max() <= 1e-4
+        assert abs(r["chi2"][b] - ref["chi2"]) <= chi2_tol(o, ref["match_xy"], 1e-4) + \
+            1e-12 * ref["chi2"]
+
+
+def tri_nodes(grid, tri):
+    x0, y0, dx, dy, nx, ny = grid
+    cell, t = divmod(int(tri), 2)
+    i, j = cell % (nx - 1), cell // (nx - 1)
+    v = [(i, j), (i + 1, j), (i + 1, j + 1)] if t == 0 else [(i, j), (i + 1, j + 1), (i, j + 1)]
+    return [(x0 + a * dx, y0 + b * dy) for a, b in v]
+
+
+def test_c5_full_size_local_checks(oracle):
+    w = W.c5(batch=2)
+    o = load_obs("c5")
+    grid = w.grids[0].as_tuple()
+    # 100 systems in a strongly folded lens: size the per-sample lists for it
+    r = run(w, o, [grid] * w.batch, lt.MIXED, grad=True, capacity=1 << 17)
+    print("c5 stats", r["stats"])
+    ox, oy = np.asarray(o["x"]), np.asarray(o["y"])
+    sys_, rr = np.asarray(o["sys"]), np.asarray(o["dls_ds"])
+    for b in range(w.batch):
+        p = w.params[b]
+        bary, _ = oracle.barycentres(p, o)
+        np.testing.assert_allclose(r["bary"][b], bary, rtol=0, atol=1e-10)
+        for m in range(len(ox)):
+            tri = r["mt"][b, m]
+            if tri < 0:
+                continue
+            V = tri_nodes(grid, tri)
+            i = sys_[m]
+            # the oracle's own FP64 predicate on this triangle alone
+            H, U = oracle.find_images(p, (V[0][0], V[0][1], grid[2], grid[3], 2, 2),
+                                      [bary[i]], [rr[i]])
+            t_local = 0 if tri % 2 == 0 else 1
+            got = [h for h in H if h["tri"] == t_local]
+            assert len(got) == 1 and not U, (b, m, tri)
+            assert abs(got[0]["x"] - r["mxy"][b, m, 0]) <= 1e-4
+            assert abs(got[0]["y"] - r["mxy"][b, m, 1]) <= 1e-4
+    # sampled deflections of sample 0 within their bound
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params[:1])
+    a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+    rng = np.random.default_rng(55)
+    idx = rng.integers(0, grid[4] * grid[5], 500)
+    jj, ii = np.divmod(idx, grid[4])
+    ax, ay, _ = oracle.alpha_points(w.params[0], grid[0] + ii * grid[2], grid[1] + jj * grid[3])
+    A = a.reshape(-1, 2).cpu().numpy()[idx].astype(np.float64)
+    E = e.reshape(-1).cpu().numpy()[idx].astype(np.float64)
+    assert np.all(np.maximum(np.abs(A[:, 0] - ax), np.abs(A[:, 1] - ay)) <= E)
+    m.close()
+    # sampled gradient components of sample 0 against central differences
+    g = r["grad"][0]
+    mt = r["mt"][0]
+    p = w.params[0]
+    rows = [1, 2, 3, 4, 5, 7]
+    big = np.argsort(-p[7])[:3]  # the most massive potentials
+    for k in list(big) + [int(rng.integers(0, w.n_pot))]:
+        for c in (0, 1, 5):
+            row = rows[c]
+            h = 1e-6 * max(abs(p[row, k]), 1e-2)
+            pp, pm = p.copy(), p.copy()
+            pp[row, k] += h
+            pm[row, k] -= h
+            fd = (oracle.chi2_frozen(pp, grid, o, mt) - oracle.chi2_frozen(pm, grid, o, mt)) / (2 * h)
+            floor = 1e-6 * np.abs(g).max()
+            assert abs(g[k, c] - fd) <= 1e-3 * abs(fd) + floor, (k, c, g[k, c], fd)

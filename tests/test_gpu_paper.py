@@ -78,3 +78,61 @@ def test_general_sie_outside_dp_patch(oracle, scale):
     dy = np.abs(grid[1] + jj * h - cy) / h
     outside = np.maximum(dx, dy) >= sep
     assert err[outside].max() <= case["bound"], (err[outside].max(), case["bound"])
+
+
+def test_paper_mixed_rule(oracle):
+    """The paper's mixed rule (Sect. 3.3, App. A.3.2) on a crop of its benchmark
+    lens: FP64 at every node of the halo patches and where the distortion
+    criteria fire on the FP32 grid, FP32 elsewhere; every node within the
+    paper's total single-precision bound of 2.3e-3"."""
+    from paper_1902_03252_gb300 import workloads as W
+    w = W.hff()
+    p = w.params[0]
+    h = 0.03
+    n = 1500
+    cx, cy = p[1, 0], p[2, 0]  # centre the crop on the first cluster halo
+    i0 = int(round(cx / h)) - n // 2
+    j0 = int(round(cy / h)) - n // 2
+    grid = (i0 * h, j0 * h, h, h, n, n)
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    a32 = m.deflect_grid(grid, precision=lt.MIXED).cpu().numpy()
+    ap, flag = m.deflect_grid(grid, precision=lt.PAPER, with_error=True)
+    ap, flag = ap.cpu().numpy(), flag.cpu().numpy() > 0.5
+    st, stats = m.sync()
+    assert st == lt.LT_OK
+    # expected flags: halo patches (closed form) and the criteria on the FP32 grid
+    exp = np.zeros((n, n), bool)
+    b0 = 4 * math.pi * (p[7] / C_KMS) ** 2 * ARCSEC
+    for k in range(p.shape[1]):
+        half = 200 if b0[k] >= 1.0 else 10
+        ic, jc = int(round((p[1, k] - grid[0]) / h)), int(round((p[2, k] - grid[1]) / h))
+        exp[max(jc - half, 0):max(min(jc + half, n), 0), max(ic - half, 0):max(min(ic + half, n), 0)] = True
+    a1, a2 = a32[..., 0], a32[..., 1]
+    hf = np.float32(h)
+    t12, t34 = np.float32(0.0092) * hf / np.float32(0.03), np.float32(0.0104) * hf / np.float32(0.03)
+    d1 = a1[1:, 1:] - a1[1:, :-1]
+    d2 = a2[1:, 1:] - a2[:-1, 1:]
+    d3 = a1[1:, 1:] - a1[:-1, 1:]
+    d4 = a2[1:, 1:] - a2[1:, :-1]
+    crit = (np.abs(hf - d1) < t12) | (np.abs(hf - d2) < t12) | (np.abs(d3) > t34) | (np.abs(d4) > t34)
+    exp[1:, 1:] |= crit
+    assert np.array_equal(flag, exp), (flag.sum(), exp.sum())
+    assert stats["fp64_nodes"] == int(exp.sum())
+    # unflagged nodes are the FP32 values, flagged ones the FP64 evaluation
+    np.testing.assert_array_equal(ap[~flag], a32[~flag].astype(np.float64))
+    rng = np.random.default_rng(9)
+    fj, fi = np.nonzero(flag)
+    sel = rng.choice(len(fi), min(1500, len(fi)), replace=False)
+    x, y = grid[0] + fi[sel] * h, grid[1] + fj[sel] * h
+    rx, ry, asum = oracle.alpha_points(p, x, y)
+    d = np.maximum(np.abs(ap[fj[sel], fi[sel], 0] - rx), np.abs(ap[fj[sel], fi[sel], 1] - ry))
+    assert np.all(d <= 1e-12 * (asum + 1.0))
+    # every node within the paper's total bound for the mixed algorithm
+    g = json.load(open(GOLDEN))
+    uj, ui = np.nonzero(~flag)
+    sel = rng.choice(len(ui), 3000, replace=False)
+    x, y = grid[0] + ui[sel] * h, grid[1] + uj[sel] * h
+    rx, ry, _ = oracle.alpha_points(p, x, y)
+    d = np.maximum(np.abs(ap[uj[sel], ui[sel], 0] - rx), np.abs(ap[uj[sel], ui[sel], 1] - ry))
+    assert d.max() <= g["total_sp_bound"], d.max()

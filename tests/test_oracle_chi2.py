@@ -1,4 +1,4 @@
-"""Pins of the oracle's barycentres, chi^2 (Eq. 8) and frozen-assignment
+"""Pins of the oracle's barycentres, chi^2 (Eq. 11) and frozen-assignment
 gradient.
 
 * barycentres of SIS images follow from |alpha| = theta_E (Sect. 2.1);

@@ -25,7 +25,7 @@ def one(kind, x=0.0, y=0.0, e=0.0, phi=0.0, rc=0.0, rcut=0.0, sv=500.0):
 
 
 def test_sis_constant_magnitude(oracle):
-    """|alpha| = theta_E everywhere but the centre (Sect. 2.1, Eq. 7)."""
+    """|alpha| = theta_E everywhere but the centre (Sect. 2.1, Eq. 10)."""
     rng = np.random.default_rng(1)
     p = one(0, 3.0, -2.0, sv=812.0)
     x, y = rng.uniform(-80, 80, (2, 500))
