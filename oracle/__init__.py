@@ -76,6 +76,10 @@ def lib():
         L.lto_chi2_grad.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double,
                                     C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, ip,
                                     C.c_int, dp, lp, dp, dp]
+        L.lto_jacobian_points.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
+        L.lto_chi2_source.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp, ip, C.c_int, dp, dp, dp]
+        L.lto_tri_magnification.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                            C.c_double, C.c_int, C.c_int, C.c_int, lp, dp, dp]
         _lib = L
     return _lib
 
@@ -221,6 +225,43 @@ def chi2_grad(params, grid, obs, match_tri):
     lib().lto_chi2_grad(pp, p.shape[1], x0, y0, dx, dy, nx, ny, ox.size, oxp, oyp, sgp, osp,
                         r.size, rp, mtp, C.byref(c2), gp)
     return c2.value, g
+
+
+def jacobian_points(params, x, y):
+    """d alpha / d theta at points: [n][2][2] (rows alpha_x, alpha_y)."""
+    p, pp = _d(_params(params))
+    x, xp = _d(np.atleast_1d(x))
+    y, yp = _d(np.atleast_1d(y))
+    j, jp = _d(np.zeros((x.size, 2, 2)))
+    lib().lto_jacobian_points(pp, p.shape[1], x.size, xp, yp, jp)
+    return j
+
+
+def chi2_source(params, obs):
+    """Source-plane chi^2 of one sample and the point magnification mu at
+    every observed image."""
+    p, pp = _d(_params(params))
+    ox, oxp = _d(obs["x"])
+    oy, oyp = _d(obs["y"])
+    sg, sgp = _d(obs["sigma"])
+    osys, osp = _i(obs["sys"])
+    r, rp = _d(obs["dls_ds"])
+    mu, mup = _d(np.zeros(ox.size))
+    c2 = C.c_double(0.0)
+    lib().lto_chi2_source(pp, p.shape[1], ox.size, oxp, oyp, sgp, osp, r.size, rp,
+                          C.byref(c2), mup)
+    return c2.value, mu
+
+
+def tri_magnification(params, grid, tri, r):
+    """Signed triangle magnification (image area / lensed area) of grid triangles."""
+    x0, y0, dx, dy, nx, ny = grid
+    p, pp = _d(_params(params))
+    t, tp = _l(np.atleast_1d(tri))
+    rr, rp = _d(np.broadcast_to(np.asarray(r, dtype=np.float64), t.shape))
+    mu, mup = _d(np.zeros(t.size))
+    lib().lto_tri_magnification(pp, p.shape[1], x0, y0, dx, dy, nx, ny, t.size, tp, rp, mup)
+    return mu
 
 
 def dls_ds(z_l, z_s, omega_m=0.3, omega_lambda=0.7):

@@ -25,6 +25,12 @@
  *      observed image matched to the nearest predicted image of its system.
  *   7. d chi^2 / d(params) with the triangle assignment and matching frozen,
  *      by forward-mode dual numbers through the same templated code.
+ *   8. magnifications and the source-plane chi^2 (extensions the relensing
+ *      pipeline of Fig. 1 motivates): the deflection Jacobian d alpha/d theta
+ *      by dual numbers (alpha depends on theta only through theta - c, so it
+ *      is minus the derivative w.r.t. the potential centre), the point
+ *      magnification 1/det(I - r d alpha/d theta), and the triangle
+ *      magnification (image-plane area over lensed source-plane area).
  *
  * Readings where the paper is silent (the PIEMD profile, grid placement,
  * cell diagonal, tie rule, matching, penalty) are the ones listed in the
@@ -575,6 +581,92 @@ int lto_chi2_frozen(const double* params, int n_pot, double x0, double y0, doubl
   Grid g{x0, y0, dx, dy, nx, ny};
   *chi2 = chi2_frozen<double>(params, n_pot, g, n_obs, ox, oy, osig, osys, n_sys, sys_r,
                               match_tri);
+  return 0;
+}
+
+/*
+ * Deflection Jacobian J = d alpha / d theta at n points, jac[m] = (J_xx, J_xy,
+ * J_yx, J_yy).  Forward-mode duals: seeding the centre row (x, then y) of
+ * every potential at once gives sum_k d alpha_k / d c_k = -J, because each
+ * alpha_k depends on theta and c_k only through theta - c_k.
+ */
+int lto_jacobian_points(const double* params, int n_pot, int n, const double* x,
+                        const double* y, double* jac) {
+  std::vector<Dual> p(N_ROWS * (size_t)n_pot);
+  for (int m = 0; m < n; ++m) {
+    for (int col = 0; col < 2; ++col) {  // derivative w.r.t. theta_x, then theta_y
+      for (size_t t = 0; t < p.size(); ++t) p[t] = Dual(params[t], 0.0);
+      const int row = col == 0 ? R_X : R_Y;
+      for (int k = 0; k < n_pot; ++k) p[(size_t)row * n_pot + k].d = 1.0;
+      Dual ax, ay;
+      alpha_total(p.data(), n_pot, x[m], y[m], ax, ay, nullptr);
+      jac[4 * m + col] = -ax.d;      // J_xx, J_xy
+      jac[4 * m + 2 + col] = -ay.d;  // J_yx, J_yy
+    }
+  }
+  return 0;
+}
+
+/*
+ * Source-plane chi^2 of one sample (the LENSTOOL source-plane fit of Jullo et
+ * al. 2007, which the paper cites for the chi^2): for every observed image m
+ * of system i, beta_m = theta_m - r_i alpha(theta_m) (Eq. 13), the system's
+ * barycentre as in step 3, and
+ *   chi^2_S = sum_m |beta_m - beta_bar_i|^2 mu_m^2 / sigma_m^2,
+ *   mu_m = 1 / det(I - r_i J(theta_m)),
+ * i.e. the image-plane error budget carried to the source plane by the local
+ * magnification.  mu[n_obs] receives mu_m.
+ */
+int lto_chi2_source(const double* params, int n_pot, int n_obs, const double* ox,
+                    const double* oy, const double* osig, const int32_t* osys, int n_sys,
+                    const double* sys_r, double* chi2, double* mu) {
+  std::vector<double> bary(2 * (size_t)n_sys), jac(4 * (size_t)n_obs);
+  lto_barycentres(params, n_pot, n_obs, ox, oy, osys, n_sys, sys_r, bary.data(), nullptr);
+  lto_jacobian_points(params, n_pot, n_obs, ox, oy, jac.data());
+  double c2 = 0.0;
+  for (int m = 0; m < n_obs; ++m) {
+    const int i = osys[m];
+    const double r = sys_r[i];
+    double ax, ay;
+    alpha_total(params, n_pot, ox[m], oy[m], ax, ay, nullptr);
+    const double bx = ox[m] - r * ax, by = oy[m] - r * ay;
+    const double* J = &jac[4 * (size_t)m];
+    const double det = (1.0 - r * J[0]) * (1.0 - r * J[3]) - (r * J[1]) * (r * J[2]);
+    const double u = 1.0 / det;
+    mu[m] = u;
+    const double ex = bx - bary[2 * i], ey = by - bary[2 * i + 1];
+    c2 = c2 + (ex * ex + ey * ey) * u * u / (osig[m] * osig[m]);
+  }
+  *chi2 = c2;
+  return 0;
+}
+
+/*
+ * Triangle magnification of the triangles tri[n] of a grid (numbering as in
+ * step 4): the signed image-plane area divided by the signed area of the
+ * triangle lensed with ratio r[n] (Eq. 13).  Negative for images of odd
+ * parity; +-inf where the lensed triangle is degenerate.
+ */
+int lto_tri_magnification(const double* params, int n_pot, double x0, double y0, double dx,
+                          double dy, int nx, int ny, int n, const int64_t* tri, const double* r,
+                          double* mu) {
+  Grid g{x0, y0, dx, dy, nx, ny};
+  for (int m = 0; m < n; ++m) {
+    int64_t node[3];
+    tri_nodes(g, tri[m], node);
+    double tx[3], ty[3], bx[3], by[3];
+    for (int v = 0; v < 3; ++v) {
+      tx[v] = g.X((int)(node[v] % nx));
+      ty[v] = g.Y((int)(node[v] / nx));
+      double ax, ay;
+      alpha_total(params, n_pot, tx[v], ty[v], ax, ay, nullptr);
+      bx[v] = tx[v] - r[m] * ax;
+      by[v] = ty[v] - r[m] * ay;
+    }
+    const double area_img = (tx[1] - tx[0]) * (ty[2] - ty[0]) - (ty[1] - ty[0]) * (tx[2] - tx[0]);
+    const double area_src = (bx[1] - bx[0]) * (by[2] - by[0]) - (by[1] - by[0]) * (bx[2] - bx[0]);
+    mu[m] = area_img / area_src;
+  }
   return 0;
 }
 
