@@ -270,6 +270,33 @@ lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot, const lt_
                                   float* alpha_out, float* err_out, int32_t* status_out,
                                   uintptr_t stream);
 
+/* Source-plane chi^2 of every sample: each observed image is mapped to the
+ * source plane (beta = theta - (D_ls/D_s) alpha, Eq. 13) and each system's
+ * barycentre formed as in lt_chi2 (Fig. 1); the scatter about it is weighted
+ * by the squared point magnification at the observed image,
+ *   chi2_S = sum_m |beta_m - beta_bar|^2 mu_m^2 / sigma_m^2,
+ *   mu_m = 1 / det(I - (D_ls/D_s) d alpha/d theta),
+ * the LENSTOOL source-plane fit (Jullo et al. 2007, which the paper cites for
+ * the chi^2).  d alpha/d theta is the sum of closed-form second derivatives
+ * of every potential.  FP64 throughout; needs no grid.
+ * obs: host struct of device pointers; chi2_out: device [batch] double;
+ * mu_out: device [batch][n_obs] double (the point magnifications) or NULL.
+ * Errors: LT_ERR_INVALID_ARG. */
+lt_status lt_chi2_source(lt_model* model, const lt_obs* obs, double* chi2_out, double* mu_out,
+                         uintptr_t stream);
+
+/* Signed triangle magnification of the predicted image each observed image
+ * was matched to in the last lt_chi2 / lt_chi2_grad / lt_chi2_graph call: the
+ * image-plane area of the grid triangle over the signed area of the triangle
+ * lensed into the source plane (Fig. 1), from FP64 deflections of its three
+ * nodes; negative for images of odd parity; NaN for an observed image without
+ * a match.  Uses the model's current parameters: call it before
+ * lt_model_set_params changes them.  obs: the same observations as that call
+ * (host struct of device pointers); mu_out: device [batch][n_obs] double.
+ * Errors: LT_ERR_INVALID_ARG (no evaluation yet, or other observations). */
+lt_status lt_last_magnifications(lt_model* model, const lt_obs* obs, double* mu_out,
+                                 uintptr_t stream);
+
 /* D_ls/D_s of a source at redshift z_s behind a lens at z_l (Sect. 4: the
  * paper's benchmark puts the lens at 0.3 and the sources at 2.0 in flat
  * LambdaCDM, Omega_m = 0.3, Omega_Lambda = 0.7), the ratio that scales the

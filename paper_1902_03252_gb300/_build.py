@@ -23,6 +23,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 PER_FILE = {
     "lt_fp64.cu": ["-fmad=false"],
     "lt_adjoint.cu": [],
+    "lt_magnify.cu": ["-fmad=false"],
     # subnormal FP32 values never occur on the deflection / search path; with
     # flush-to-zero the MUFU approximations (rsqrt, rcp, lg2) are single
     # instructions instead of range-checked sequences

@@ -83,6 +83,11 @@ struct lt_model {
   AdjPt* d_adj_pts = nullptr;   // adjoint points (x, y, coefficient) [batch][4 n_obs]
   int obs_alloc = 0, sys_alloc = 0;
   int last_nobs = -1, last_nsys = -1;
+  // source-plane chi^2 scratch: beta and mu [batch][n_obs], barycentres [batch][n_sys]
+  double2* d_src_beta = nullptr;
+  double* d_src_mu = nullptr;
+  double2* d_src_bary = nullptr;
+  int src_obs_alloc = 0, src_sys_alloc = 0;
   // CUDA graph cache of lt_chi2_graph
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -517,7 +522,8 @@ void lt_model_destroy(lt_model* m) {
   void* ptrs[] = {m->d_params, m->d_pot64, m->d_pot32, m->d_seg, m->d_status, m->d_counters,
                   m->d_nodes, m->d_hits, m->d_work, m->d_hit_count, m->d_work_count,
                   m->d_plan_grids, m->d_plan_items, m->d_beta_obs, m->d_bary, m->d_match_tri,
-                  m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched};
+                  m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched,
+                  m->d_src_beta, m->d_src_mu, m->d_src_bary};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -732,6 +738,49 @@ lt_status lt_chi2_grad(lt_model* m, const lt_grid* grids, const lt_obs* obs,
   LT_CUDA(launch_adjoint(m->d_pot64, m->n_pot, m->batch, m->d_plan_grids, m->d_hits,
                          m->hits_cap_alloc, *obs, m->d_match_hit, m->d_adj_lam, m->d_adj_pts,
                          grad_out, m->sm_count, st));
+  return LT_OK;
+}
+
+lt_status lt_chi2_source(lt_model* m, const lt_obs* obs, double* chi2_out, double* mu_out,
+                         uintptr_t stream) {
+  if (!m) return LT_ERR_INVALID_ARG;
+  LT_CHECK_ARG(chi2_out != nullptr, "chi2_out is NULL");
+  lt_status s = check_obs(m, obs);
+  if (s != LT_OK) return s;
+  cudaStream_t st = S(stream);
+  if (obs->n_obs > m->src_obs_alloc) {
+    if (m->d_src_beta) LT_CUDA(cudaFree(m->d_src_beta));
+    if (m->d_src_mu) LT_CUDA(cudaFree(m->d_src_mu));
+    m->d_src_beta = nullptr;
+    m->d_src_mu = nullptr;
+    LT_CUDA(cudaMalloc(&m->d_src_beta, sizeof(double2) * (size_t)m->batch * obs->n_obs));
+    LT_CUDA(cudaMalloc(&m->d_src_mu, sizeof(double) * (size_t)m->batch * obs->n_obs));
+    m->src_obs_alloc = obs->n_obs;
+  }
+  if (obs->n_sys > m->src_sys_alloc) {
+    if (m->d_src_bary) LT_CUDA(cudaFree(m->d_src_bary));
+    m->d_src_bary = nullptr;
+    LT_CUDA(cudaMalloc(&m->d_src_bary, sizeof(double2) * (size_t)m->batch * obs->n_sys));
+    m->src_sys_alloc = obs->n_sys;
+  }
+  double* mu = mu_out ? mu_out : m->d_src_mu;
+  LT_CUDA(launch_chi2_source(m->d_pot64, m->n_pot, m->batch, *obs, m->d_src_beta, mu,
+                             m->d_src_bary, chi2_out, m->sm_count, st));
+  return LT_OK;
+}
+
+lt_status lt_last_magnifications(lt_model* m, const lt_obs* obs, double* mu_out,
+                                 uintptr_t stream) {
+  if (!m) return LT_ERR_INVALID_ARG;
+  LT_CHECK_ARG(mu_out != nullptr, "mu_out is NULL");
+  LT_CHECK_ARG(m->last_nobs > 0, "no chi^2 evaluation has run");
+  lt_status s = check_obs(m, obs);
+  if (s != LT_OK) return s;
+  LT_CHECK_ARG(obs->n_obs == m->last_nobs && obs->n_sys == m->last_nsys,
+               "obs differ from the last chi^2 evaluation's");
+  LT_CUDA(launch_mag_pred(m->d_pot64, m->n_pot, m->batch, m->d_plan_grids, m->d_hits,
+                          m->hits_cap_alloc, *obs, m->d_match_hit, mu_out, m->sm_count,
+                          S(stream)));
   return LT_OK;
 }
 

@@ -308,6 +308,17 @@ cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const Sampl
                            const Hit* hits, int64_t hit_cap, const lt_obs& obs,
                            const int32_t* match_hit, double2* lam, AdjPt* pts, double* grad,
                            int sm_count, cudaStream_t st);
+// Source-plane chi^2: beta and point magnification per (sample, observed
+// image), then barycentres and chi^2 per sample.  beta, mu: [batch][n_obs];
+// bary: [batch][n_sys]; chi2: [batch].
+cudaError_t launch_chi2_source(const Pot64* pot64, int n_pot, int batch, const lt_obs& obs,
+                               double2* beta, double* mu, double2* bary, double* chi2,
+                               int sm_count, cudaStream_t st);
+// Triangle magnification of each observed image's matched predicted image.
+cudaError_t launch_mag_pred(const Pot64* pot64, int n_pot, int batch, const SampleGrid* grids,
+                            const Hit* hits, int64_t hit_cap, const lt_obs& obs,
+                            const int32_t* match_hit, double* mu, int sm_count,
+                            cudaStream_t st);
 // The paper's mixed rule for a deflection grid (LT_PREC_PAPER).
 cudaError_t launch_paper_flags(const float4* nodes, const Pot64* pot64, int n_pot,
                                const lt_grid& g, double2* out, unsigned char* flags,

@@ -25,7 +25,8 @@ POS_TOL = 2.5e-5
 EXPORTED = ("lt_model_create", "lt_model_destroy", "lt_last_error", "lt_status_string",
             "lt_model_set_params", "lt_deflect_grid", "lt_find_images", "lt_chi2",
             "lt_chi2_grad", "lt_last_matches", "lt_model_sync", "lt_chi2_graph",
-            "lt_autotune", "lt_profile_enable", "lt_profile_read", "lt_dls_ds", "lt_version")
+            "lt_autotune", "lt_profile_enable", "lt_profile_read", "lt_dls_ds",
+            "lt_chi2_source", "lt_last_magnifications", "lt_version")
 
 
 class Grid(C.Structure):
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = False):
     L.lt_chi2_graph.argtypes = [vp, C.POINTER(Grid), C.POINTER(Obs), st, vp, up]
     L.lt_chi2_grad.argtypes = [vp, C.POINTER(Grid), C.POINTER(Obs), st, vp, vp, up]
     L.lt_last_matches.argtypes = [vp, vp, vp, vp, up]
+    L.lt_chi2_source.argtypes = [vp, C.POINTER(Obs), vp, vp, up]
+    L.lt_last_magnifications.argtypes = [vp, C.POINTER(Obs), vp, up]
     L.lt_model_sync.argtypes = [vp, up, C.POINTER(Stats)]
     L.lt_autotune.argtypes = [vp, C.POINTER(Grid), up, C.POINTER(i32)]
     L.lt_profile_enable.argtypes = [vp, C.c_int]
@@ -121,7 +124,8 @@ def load(build_if_missing: bool = False):
                                             "lt_chi2_graph", "lt_chi2_grad", "lt_last_matches",
                                             "lt_model_sync", "lt_autotune",
                                             "lt_profile_enable", "lt_profile_read",
-                                            "lt_dls_ds"):
+                                            "lt_dls_ds", "lt_chi2_source",
+                                            "lt_last_magnifications"):
             f.restype = st
     _lib = L
     return L
@@ -207,7 +211,8 @@ class Model:
         """params: [batch][8][n_pot] float64 (numpy on the host or a CUDA tensor)."""
         torch = _torch()
         if isinstance(params, torch.Tensor) and params.is_cuda:
-            p = params.to(torch.float64).contiguous()
+            p = params.detach().to(torch.float64).contiguous()
+            assert tuple(p.shape) == (self.batch, N_ROWS, self.n_pot), tuple(p.shape)
             self._keep = p
             self._check(self._lib.lt_model_set_params(self.h, _ptr(p), 1, _stream(stream)),
                         "lt_model_set_params")
@@ -266,6 +271,24 @@ class Model:
                                            _ptr(c2), _ptr(gr), _stream(stream)), "lt_chi2_grad")
         return c2, gr
 
+    def chi2_source(self, obs: Observations, stream=None):
+        """Source-plane chi^2 [batch] and point magnifications [batch][n_obs]."""
+        torch = _torch()
+        c2 = torch.empty((self.batch,), dtype=torch.float64, device="cuda")
+        mu = torch.empty((self.batch, int(obs.x.numel())), dtype=torch.float64, device="cuda")
+        self._check(self._lib.lt_chi2_source(self.h, C.byref(obs.c_struct()), _ptr(c2), _ptr(mu),
+                                             _stream(stream)), "lt_chi2_source")
+        return c2, mu
+
+    def last_magnifications(self, obs: Observations, stream=None):
+        """Signed triangle magnification of each observed image's matched
+        predicted image in the last chi^2 evaluation [batch][n_obs] (NaN: no match)."""
+        torch = _torch()
+        mu = torch.empty((self.batch, int(obs.x.numel())), dtype=torch.float64, device="cuda")
+        self._check(self._lib.lt_last_magnifications(self.h, C.byref(obs.c_struct()), _ptr(mu),
+                                                     _stream(stream)), "lt_last_magnifications")
+        return mu
+
     def last_matches(self, n_obs, n_sys, stream=None):
         torch = _torch()
         mt = torch.empty((self.batch, n_obs), dtype=torch.int64, device="cuda")
@@ -300,6 +323,52 @@ class Model:
         self._check(self._lib.lt_autotune(self.h, grids_array([grid]), _stream(stream),
                                           C.byref(ch)), "lt_autotune")
         return ch.value
+
+
+# parameter rows that the adjoint differentiates, in its column order:
+# x, y, e, phi, r_core, sigma_v
+GRAD_ROWS = (1, 2, 3, 4, 5, 7)
+_chi2_fn = None
+
+
+def _chi2_function():
+    global _chi2_fn
+    if _chi2_fn is None:
+        torch = _torch()
+
+        class Chi2(torch.autograd.Function):
+            """chi^2 of every sample as a differentiable function of the
+            parameter tensor; the backward pass is the library's adjoint
+            (lt_chi2_grad, triangle assignment held fixed)."""
+
+            @staticmethod
+            def forward(ctx, params, model, grids, obs, precision):
+                model.set_params(params)
+                if ctx.needs_input_grad[0]:
+                    c2, g = model.chi2_grad(grids, obs, precision=precision)
+                    ctx.save_for_backward(g)
+                else:
+                    c2 = model.chi2(grids, obs, precision=precision)
+                return c2
+
+            @staticmethod
+            def backward(ctx, gout):
+                (g,) = ctx.saved_tensors  # [batch][n_pot][6]
+                b, n_pot, _ = g.shape
+                gp = torch.zeros((b, N_ROWS, n_pot), dtype=torch.float64, device=g.device)
+                gp[:, list(GRAD_ROWS), :] = (g * gout.to(g.dtype)[:, None, None]).transpose(1, 2)
+                return gp, None, None, None, None
+
+        _chi2_fn = Chi2
+    return _chi2_fn
+
+
+def chi2_autograd(model, params, grids, obs, precision=MIXED):
+    """chi^2 [batch] of ``params`` ([batch][8][n_pot] float64 CUDA tensor) with
+    autograd support.  Gradients flow to the rows x, y, e, phi, r_core and
+    sigma_v; kind (discrete) and r_cut are held constant (their gradient is
+    zero)."""
+    return _chi2_function().apply(params, model, grids, obs, precision)
 
 
 def dls_ds(z_l: float, z_s: float, omega_m: float = 0.3, omega_lambda: float = 0.7) -> float:
