@@ -225,6 +225,14 @@ lt_status lt_model_sync(lt_model* model, uintptr_t stream, lt_stats* stats);
 lt_status lt_chi2_graph(lt_model* model, const lt_grid* grids, const lt_obs* obs,
                         lt_precision precision, double* chi2_out, uintptr_t stream);
 
+/* Choose the launch shape of the FP32 deflection kernel by index, in
+ * [0, lt_num_shapes()): (threads per block, nodes per thread) of
+ * (256, 2), (256, 4), (128, 4), (128, 8).  Every shape computes the same
+ * quantities within the same error bound; only speed differs.  lt_autotune
+ * picks one by timing.  Errors: LT_ERR_INVALID_ARG. */
+lt_status lt_model_set_shape(lt_model* model, int32_t shape);
+int32_t lt_num_shapes(void);
+
 /* Autotune the FP32 deflection kernel's launch shape for this model's
  * potential mix on a representative grid (times each candidate with CUDA
  * events on `stream`) and keep the fastest for later calls.  *choice

@@ -190,6 +190,19 @@ bool same_grids(const std::vector<lt_grid>& a, const lt_grid* b, int n) {
   return std::memcmp(a.data(), b, sizeof(lt_grid) * n) == 0;
 }
 
+// Device description of one sample's grid whose nodes start at node_off.
+SampleGrid sample_grid(const lt_grid& g, int64_t node_off) {
+  SampleGrid s;
+  s.x0 = g.x0; s.y0 = g.y0; s.dx = g.dx; s.dy = g.dy; s.nx = g.nx; s.ny = g.ny;
+  s.node_off = node_off;
+  const double tm = std::max(std::max(std::fabs(g.x0), std::fabs(g.x0 + (g.nx - 1) * g.dx)),
+                             std::max(std::fabs(g.y0), std::fabs(g.y0 + (g.ny - 1) * g.dy)));
+  s.theta_max = (float)(tm * (1.0 + 1e-6));
+  s.pad = 0.f;
+  s.x0f = (float)g.x0; s.y0f = (float)g.y0; s.dxf = (float)g.dx; s.dyf = (float)g.dy;
+  return s;
+}
+
 int64_t defl_item_nodes(int precision, int shape) {
   if (precision == LT_PREC_FP64) return kDefl64Nodes;
   DeflectShape sh = deflect_shape(shape);
@@ -224,13 +237,7 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
       size_t nb = (size_t)grids[b].nx * grids[b].ny;
       if (b > c.b0 && nodes + nb > budget_nodes) break;
       const lt_grid& g = grids[b];
-      SampleGrid& s = sg[b];
-      s.x0 = g.x0; s.y0 = g.y0; s.dx = g.dx; s.dy = g.dy; s.nx = g.nx; s.ny = g.ny;
-      s.node_off = (int64_t)nodes;
-      double tm = std::max(std::max(std::fabs(g.x0), std::fabs(g.x0 + (g.nx - 1) * g.dx)),
-                           std::max(std::fabs(g.y0), std::fabs(g.y0 + (g.ny - 1) * g.dy)));
-      s.theta_max = (float)(tm * (1.0 + 1e-6));
-      s.pad = 0.f;
+      sg[b] = sample_grid(g, (int64_t)nodes);
       nodes += nb;
       ++b;
     }
@@ -567,13 +574,7 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   cudaStream_t st = S(stream);
   // a one-sample plan over the caller's grid (does not disturb the batch plan)
   const lt_grid& g = *grid;
-  SampleGrid sg;
-  sg.x0 = g.x0; sg.y0 = g.y0; sg.dx = g.dx; sg.dy = g.dy; sg.nx = g.nx; sg.ny = g.ny;
-  sg.node_off = 0;
-  double tm = std::max(std::max(std::fabs(g.x0), std::fabs(g.x0 + (g.nx - 1) * g.dx)),
-                       std::max(std::fabs(g.y0), std::fabs(g.y0 + (g.ny - 1) * g.dy)));
-  sg.theta_max = (float)(tm * (1.0 + 1e-6));
-  sg.pad = 0.f;
+  const SampleGrid sg = sample_grid(g, 0);
   const int64_t nodes = (int64_t)g.nx * g.ny;
   LT_CHECK_ARG(precision != LT_PREC_PAPER || nodes < ((int64_t)1 << 31),
                "LT_PREC_PAPER grids are limited to 2^31 nodes");
@@ -851,6 +852,18 @@ lt_status lt_profile_read(lt_model* m, lt_profile* out, int reset) {
   if (reset) m->prof_acc = lt_profile{};
   return LT_OK;
 }
+
+lt_status lt_model_set_shape(lt_model* m, int32_t shape) {
+  if (!m) return LT_ERR_INVALID_ARG;
+  LT_CHECK_ARG(shape >= 0 && shape < kNumShapes, "shape out of range");
+  if (m->shape != shape) {
+    m->shape = shape;
+    m->plan.grids.clear();  // item sizes depend on the shape
+  }
+  return LT_OK;
+}
+
+int32_t lt_num_shapes(void) { return kNumShapes; }
 
 lt_status lt_autotune(lt_model* m, const lt_grid* grid, uintptr_t stream, int32_t* choice) {
   if (!m) return LT_ERR_INVALID_ARG;

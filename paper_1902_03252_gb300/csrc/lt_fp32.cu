@@ -271,22 +271,21 @@ __global__ void __launch_bounds__(kSearchThreads)
                Hit* __restrict__ hits, int64_t hit_cap, Work64* __restrict__ work,
                int64_t work_cap, unsigned long long* hit_count, unsigned long long* work_count,
                long long* counters, uint32_t* status,
-               unsigned long long* __restrict__ next_item) {
+               unsigned long long* __restrict__ /*next_item: unused, static items*/) {
   constexpr int kStrips = kSearchThreads / 32;
   __shared__ SrcSmem ss[kMaxSrcSmem];
   __shared__ StripBox sb[kStrips];
   __shared__ unsigned short surv[kStrips][kMaxSrcSmem];
   __shared__ int n_surv[kStrips];
-  __shared__ long long s_item;
   const float u = kU32;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   long long n_hit = 0, n_amb = 0, n_ref = 0;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
-    if (item >= n_items) break;
+  int staged = -1;  // sample whose whole source list is in ss (block-uniform)
+  // static distribution of the items: the search follows the deflection on
+  // the same stream, so every block starts together and the fetch latency of
+  // a shared counter would sit on each item's critical path
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __syncthreads();  // the previous item's readers of sb / surv are done
     const int b = find_sample(item_off, n_samples, item);
     const SampleGrid g = grids[b];
     const int sample = src.sample_base + b;
@@ -294,12 +293,19 @@ __global__ void __launch_bounds__(kSearchThreads)
     const int64_t cell = (item - item_off[b]) * kSearchThreads + threadIdx.x;
     const bool valid = cell < cells;
     const int64_t cl = valid ? cell : 0;
-    const int j = (int)(cl / (g.nx - 1));
-    const int i = (int)(cl - (int64_t)j * (g.nx - 1));
+    int i, j;
+    if (cells < ((int64_t)1 << 31)) {  // 32-bit index arithmetic
+      const unsigned c32 = (unsigned)cl, w32 = (unsigned)(g.nx - 1);
+      j = (int)(c32 / w32);
+      i = (int)(c32 - (unsigned)j * w32);
+    } else {
+      j = (int)(cl / (g.nx - 1));
+      i = (int)(cl - (int64_t)j * (g.nx - 1));
+    }
     const int64_t n00 = g.node_off + (int64_t)j * g.nx + i;
     const float4 v00 = nodes[n00], v10 = nodes[n00 + 1], v01 = nodes[n00 + g.nx],
                  v11 = nodes[n00 + g.nx + 1];
-    const float hx = (float)g.dx, hy = (float)g.dy, gx0 = (float)g.x0, gy0 = (float)g.y0;
+    const float hx = g.dxf, hy = g.dyf, gx0 = g.x0f, gy0 = g.y0f;
     const float hmax = fmaxf(fabsf(hx), fabsf(hy));
     const float xl = fmaf((float)i, hx, gx0);
     const float xr = fmaf((float)(i + 1), hx, gx0);
@@ -330,12 +336,16 @@ __global__ void __launch_bounds__(kSearchThreads)
     const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
     for (int s0 = 0; s0 < src.n_src; s0 += kMaxSrcSmem) {
       const int sn = min(kMaxSrcSmem, src.n_src - s0);
-      __syncthreads();
-      for (int v = threadIdx.x; v < sn; v += kSearchThreads) {
-        const float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
-        ss[v] = SrcSmem{px, py, (float)sr[s0 + v],
-                        u * (4.0f * g.theta_max + fabsf(px) + fabsf(py))};
+      const bool whole = sn == src.n_src;
+      if (!whole) __syncthreads();  // earlier chunk's readers of ss are done
+      if (!whole || staged != sample) {
+        for (int v = threadIdx.x; v < sn; v += kSearchThreads) {
+          const float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
+          ss[v] = SrcSmem{px, py, (float)sr[s0 + v],
+                          u * (4.0f * g.theta_max + fabsf(px) + fabsf(py))};
+        }
       }
+      staged = whole ? sample : -1;
       if (threadIdx.x < kStrips) n_surv[threadIdx.x] = 0;
       __syncthreads();
       // (1) one thread per (strip, source) pair

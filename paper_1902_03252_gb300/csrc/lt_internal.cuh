@@ -235,6 +235,7 @@ struct SampleGrid {
   int64_t node_off;  // offset of node (0,0) in the node workspace
   float theta_max;   // largest |coordinate| of any node
   float pad;
+  float x0f, y0f, dxf, dyf;  // x0, y0, dx, dy rounded to FP32 (once, on the host)
 };
 
 // Work item of the FP64 stage: an ambiguous (triangle, source) pair or an

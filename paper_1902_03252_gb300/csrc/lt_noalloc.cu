@@ -167,6 +167,7 @@ extern "C" lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot
                               std::fmax(std::fabs(gr.y0), std::fabs(gr.y0 + (gr.ny - 1) * gr.dy)));
   g.theta_max = (float)(tm * (1.0 + 1e-6));
   g.pad = 0.f;
+  g.x0f = (float)gr.x0; g.y0f = (float)gr.y0; g.dxf = (float)gr.dx; g.dyf = (float)gr.dy;
   const int64_t nodes = (int64_t)gr.nx * gr.ny;
   const int64_t n_items = (nodes + kNT * kNPT - 1) / (kNT * kNPT);
   int per_sm = 0;

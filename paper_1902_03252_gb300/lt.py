@@ -26,7 +26,8 @@ EXPORTED = ("lt_model_create", "lt_model_destroy", "lt_last_error", "lt_status_s
             "lt_model_set_params", "lt_deflect_grid", "lt_find_images", "lt_chi2",
             "lt_chi2_grad", "lt_last_matches", "lt_model_sync", "lt_chi2_graph",
             "lt_autotune", "lt_profile_enable", "lt_profile_read", "lt_dls_ds",
-            "lt_chi2_source", "lt_last_magnifications", "lt_version")
+            "lt_chi2_source", "lt_last_magnifications", "lt_model_set_shape",
+            "lt_num_shapes", "lt_version")
 
 
 class Grid(C.Structure):
@@ -110,6 +111,8 @@ def load(build_if_missing: bool = False):
     L.lt_chi2_grad.argtypes = [vp, C.POINTER(Grid), C.POINTER(Obs), st, vp, vp, up]
     L.lt_last_matches.argtypes = [vp, vp, vp, vp, up]
     L.lt_chi2_source.argtypes = [vp, C.POINTER(Obs), vp, vp, up]
+    L.lt_model_set_shape.argtypes = [vp, i32]
+    L.lt_num_shapes.restype = i32
     L.lt_last_magnifications.argtypes = [vp, C.POINTER(Obs), vp, up]
     L.lt_model_sync.argtypes = [vp, up, C.POINTER(Stats)]
     L.lt_autotune.argtypes = [vp, C.POINTER(Grid), up, C.POINTER(i32)]
@@ -125,7 +128,7 @@ def load(build_if_missing: bool = False):
                                             "lt_model_sync", "lt_autotune",
                                             "lt_profile_enable", "lt_profile_read",
                                             "lt_dls_ds", "lt_chi2_source",
-                                            "lt_last_magnifications"):
+                                            "lt_last_magnifications", "lt_model_set_shape"):
             f.restype = st
     _lib = L
     return L
@@ -270,6 +273,10 @@ class Model:
         self._check(self._lib.lt_chi2_grad(self.h, g, C.byref(obs.c_struct()), precision,
                                            _ptr(c2), _ptr(gr), _stream(stream)), "lt_chi2_grad")
         return c2, gr
+
+    def set_shape(self, shape: int):
+        """Pin the FP32 deflection launch shape (index into the shape table)."""
+        self._check(self._lib.lt_model_set_shape(self.h, int(shape)), "lt_model_set_shape")
 
     def chi2_source(self, obs: Observations, stream=None):
         """Source-plane chi^2 [batch] and point magnifications [batch][n_obs]."""

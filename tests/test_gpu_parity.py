@@ -92,6 +92,33 @@ def test_deflect_mixed_within_running_bound(oracle, seed):
     assert ratio.max() <= 1.0
 
 
+@pytest.mark.parametrize("shape", range(4))
+def test_deflect_every_shape_within_bound(oracle, shape):
+    """Every launch shape of the FP32 deflection on 300 potentials of all
+    three kinds -- more than one staged chunk of 256 -- over a grid whose node
+    count is not a multiple of any work item: within the running bound, and
+    the bound itself identical across shapes up to its own rounding."""
+    rng = np.random.default_rng(40 + shape)
+    p = W.draw_piemd(rng, 300, 40.0, 50.0, 900.0)
+    p[0, ::5] = W.SIS
+    p[0, 2::5] = W.SIE
+    p[3, 2::5] = rng.uniform(0, 0.3, p[3, 2::5].shape)
+    grid = (-45.0, -41.0, 90.0 / 250, 82.0 / 231, 251, 232)
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    m.set_shape(shape)
+    a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+    m.set_shape(1)
+    a1, e1 = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+    assert m.sync()[0] == lt.LT_OK
+    a, e = a.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
+    ref, _ = oracle.deflect_grid(p, grid, n_threads=4)
+    d = np.abs(a - ref).max(axis=-1)
+    assert np.all(np.isfinite(e)) and np.all(e > 0)
+    assert (d / e).max() <= 1.0, (d / e).max()
+    np.testing.assert_allclose(e, e1.cpu().numpy().astype(np.float64), rtol=1e-4)
+
+
 def test_deflect_c2_full_size_sampled(oracle):
     """The 2000^2, 100-PIEMD grid in the benchmark's launch configuration:
     every node within its bound on a sampled subset, FP64 on the same subset."""
