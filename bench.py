@@ -46,7 +46,7 @@ PIEMD_NODE_POT_PER_SM_CLK = 2.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -93,6 +93,14 @@ class Clocks:
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed region starts only once the sampler is producing rows
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
@@ -139,7 +147,7 @@ def source_sha(files) -> str:
 
 
 # the kernel sources and the build flags (-ftz etc.) they are compiled with
-DEFLECT32_SOURCES = ("lt_fp32.cu", "lt_fp32.cuh", "lt_internal.cuh", "../_build.py")
+DEFLECT32_SOURCES = ("lt_deflect32.cu", "lt_fp32.cuh", "lt_internal.cuh", "../_build.py")
 
 
 def traffic_for(kernel: str, files):
@@ -372,6 +380,8 @@ def run_ours(a, rank, world, local):
     if not a.no_extras:
         line["hff_deflection"] = extra_hff(lt, W, torch, dev)
         line["batched_c3"] = extra_batched(lt, W, torch, dev)
+        line["gradient_c4"] = extra_gradient(lt, W, torch, dev)
+        line["large_c5"] = extra_large(lt, W, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(w, o)
     if rank == 0:
@@ -445,6 +455,57 @@ def extra_batched(lt, W, torch, dev, steps=2):
     m.close()
     return {"workload": "c3: 1024 samples x 50 PIEMD, grids 500^2..2000^2, 10 systems",
             "s_per_batch": t, "chi2_evals_per_s": w.batch / t, "node_pot_per_s": npot / t,
+            "status": int(st), "stats": stats}
+
+
+def _time(fn, torch, steps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps / 1e3
+
+
+def extra_gradient(lt, W, torch, dev, steps=5):
+    """chi^2 with d chi^2/d(x, y, e, phi, r_core, sigma_v) of 100 PIEMD on the
+    1000^2 grid with 20 systems, against chi^2 alone, mixed precision."""
+    w = W.c4()
+    with open(os.path.join(ROOT, "tests", "golden", "obs_c4.json")) as f:
+        o = json.load(f)
+    grid = [w.grids[0].as_tuple()]
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    obs = lt.Observations.from_dict(o, device=dev)
+    t_val = _time(lambda: m.chi2(grid, obs, precision=lt.MIXED), torch, steps)
+    t_grad = _time(lambda: m.chi2_grad(grid, obs, precision=lt.MIXED), torch, steps)
+    st, _ = m.sync()
+    m.close()
+    return {"workload": "c4: 100 PIEMD x 6 parameters, 1000^2 grid, 20 systems",
+            "chi2_ms": t_val * 1e3, "chi2_grad_ms": t_grad * 1e3,
+            "gradient_overhead": t_grad / t_val - 1.0, "status": int(st)}
+
+
+def extra_large(lt, W, torch, dev, steps=2):
+    """One sample of the large workload: 1000 PIEMD, 4000^2 grid, 100 systems,
+    chi^2 and gradient (the full 64-sample batch is this times 64)."""
+    w = W.c5(batch=1)
+    with open(os.path.join(ROOT, "tests", "golden", "obs_c5.json")) as f:
+        o = json.load(f)
+    grid = [w.grids[0].as_tuple()]
+    m = lt.Model(w.n_pot, 1, hit_capacity=1 << 17)
+    m.set_params(w.params)
+    obs = lt.Observations.from_dict(o, device=dev)
+    t_val = _time(lambda: m.chi2(grid, obs, precision=lt.MIXED), torch, steps)
+    t_grad = _time(lambda: m.chi2_grad(grid, obs, precision=lt.MIXED), torch, steps)
+    st, stats = m.sync()
+    m.close()
+    return {"workload": "c5: 1000 PIEMD, 4000^2 grid, 100 systems, one sample",
+            "chi2_s": t_val, "chi2_grad_s": t_grad,
+            "node_pot_per_s": w.grids[0].nx * w.grids[0].ny * w.n_pot / t_val,
             "status": int(st), "stats": stats}
 
 

@@ -27,7 +27,9 @@ PER_FILE = {
     # subnormal FP32 values never occur on the deflection / search path; with
     # flush-to-zero the MUFU approximations (rsqrt, rcp, lg2) are single
     # instructions instead of range-checked sequences
-    "lt_fp32.cu": ["-ftz=true"],
+    "lt_deflect32.cu": ["-ftz=true"],
+    "lt_search32.cu": ["-ftz=true"],
+    "lt_paper32.cu": ["-ftz=true"],
     "lt_noalloc.cu": ["-ftz=true"],
     "lt_api.cu": [],
 }

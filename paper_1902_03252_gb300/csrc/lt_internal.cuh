@@ -260,6 +260,16 @@ struct Hit {
   double w[3];
 };
 
+// Sample of a work item: off[] holds each sample's first item, off[n] the total.
+__device__ __forceinline__ int find_sample(const int64_t* off, int n, int64_t item) {
+  int lo = 0, hi = n;  // off[lo] <= item < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the cudaGetLastError() value.
 cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,

@@ -1,10 +1,7 @@
-// FP32 kernels of the mixed-precision path:
-//   k_deflect32  potential-tiled deflection of every node, with a running
-//                first-order error bound per node (Sect. 2.2.2 / Algorithm 1
-//                superposition; error propagation in the style of App. A);
-//   k_search32   fused lens mapping (Eq. 13) and triangle test (Fig. 1) with
-//                a certified FP32 orientation filter; certain hits and the
-//                pairs that need FP64 are compacted by warp ballots.
+// FP32 triangle search of the mixed-precision path: k_search32, the fused lens
+// mapping (Eq. 13) and triangle test (Fig. 1) with a certified FP32
+// orientation filter; certain hits and the pairs that need FP64 are compacted
+// by warp ballots.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,159 +9,6 @@
 #include "lt_fp32.cuh"
 
 namespace lt {
-
-// Safety factor applied to the first-order error bound of every node.
-constexpr float kBoundSafety = 2.0f;
-constexpr int kChunk32 = 256;  // potentials staged in shared memory at a time
-
-__device__ __forceinline__ int find_sample(const int64_t* off, int n, int64_t item) {
-  int lo = 0, hi = n;  // off[lo] <= item < off[hi]
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (off[mid] <= item) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// --------------------------------------------------------------- deflection
-template <int NT, int NPT>
-__global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot32,
-                                                  const Seg32* __restrict__ seg, int n_pot,
-                                                  const SampleGrid* __restrict__ grids,
-                                                  const int64_t* __restrict__ item_off,
-                                                  int n_samples, int64_t n_items,
-                                                  float4* __restrict__ node_out,
-                                                  unsigned long long* __restrict__ next_item) {
-  __shared__ float4 sp[kChunk32 * 5];
-  __shared__ long long s_item;
-  for (;;) {
-    // dynamic distribution of the equal-size work items: blocks that start
-    // late (another kernel still resident on their SM) simply take fewer
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
-    if (item >= n_items) break;
-    int b = find_sample(item_off, n_samples, item);
-    const SampleGrid g = grids[b];
-    const Seg32 sg = seg[b];
-    const int64_t nodes = (int64_t)g.nx * g.ny;
-    const int64_t base = (item - item_off[b]) * (int64_t)(NT * NPT);
-        float X[NPT], Y[NPT], AX[NPT], AY[NPT], ER[NPT];
-#pragma unroll
-    for (int m = 0; m < NPT; ++m) {
-      int64_t n = base + m * NT + threadIdx.x;
-      if (n >= nodes) n = nodes - 1;
-      int j = (int)(n / g.nx);
-      int i = (int)(n - (int64_t)j * g.nx);
-      // node coordinates rounded once from FP64: error u|theta| (App. A's
-      // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
-      X[m] = (float)(g.x0 + (double)i * g.dx);
-      Y[m] = (float)(g.y0 + (double)j * g.dy);
-      AX[m] = 0.0f;
-      AY[m] = 0.0f;
-      ER[m] = 0.0f;
-    }
-    const float theta1 = g.theta_max;
-    const Pot32* pb = pot32 + (int64_t)b * n_pot;
-    for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
-      const int cn = min(kChunk32, n_pot - c0);
-      __syncthreads();
-      for (int v = threadIdx.x; v < cn * 5; v += NT) {
-        int k = v / 5, w = v - k * 5;
-        float4 val = pb[c0 + k].f[w];
-        if (w == 4) {  // translation-error coefficient for this grid
-          float4 h = pb[c0 + k].f[0];
-          val.x = val.x * (theta1 + fabsf(h.x) + fabsf(h.y));
-        }
-        sp[v] = val;
-      }
-      __syncthreads();
-      // kind segments [0, n_sis) SIS, [n_sis, n_sis + n_piemd) PIEMD, rest SIE
-      const int e_sis = min(max(sg.n_sis - c0, 0), cn);
-      const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
-      for (int k = 0; k < e_sis; ++k) {
-        const float4* f = &sp[k * 5];
-        const float P = f[4].x;
-#pragma unroll
-        for (int m = 0; m < NPT; ++m) sis32(f, P, X[m], Y[m], AX[m], AY[m], ER[m]);
-      }
-      for (int k = e_sis; k < e_pie; ++k) {
-        const float4* f = &sp[k * 5];
-        const float P = f[4].x;
-#pragma unroll
-        for (int m = 0; m < NPT; ++m) piemd32(f, P, X[m], Y[m], AX[m], AY[m], ER[m]);
-      }
-      for (int k = e_pie; k < cn; ++k) {
-        const float4* f = &sp[k * 5];
-        const float P = f[4].x;
-#pragma unroll
-        for (int m = 0; m < NPT; ++m) sie32(f, P, X[m], Y[m], AX[m], AY[m], ER[m]);
-      }
-    }
-    const float qs = sg.q_tot;
-#pragma unroll
-    for (int m = 0; m < NPT; ++m) {
-      int64_t n = base + m * NT + threadIdx.x;
-      if (n < nodes)
-        node_out[g.node_off + n] =
-            make_float4(AX[m], AY[m], kBoundSafety * kU32 * (ER[m] + qs), 0.0f);
-    }
-  }
-}
-
-template <int NT, int NPT>
-static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int n_pot,
-                                      const SampleGrid* grids, const int64_t* item_off,
-                                      int n_samples, int64_t n_items, float4* node_out,
-                                      unsigned long long* next_item, int sm_count,
-                                      cudaStream_t st) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32<NT, NPT>, NT, 0);
-  if (per_sm < 1) per_sm = 1;
-  int64_t blocks = (int64_t)sm_count * per_sm;
-  if (blocks > n_items) blocks = n_items;
-  if (blocks < 1) return cudaSuccess;
-  k_deflect32<NT, NPT><<<(unsigned)blocks, NT, 0, st>>>(pot32, seg, n_pot, grids, item_off,
-                                                          n_samples, n_items, node_out,
-                                                          next_item);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
-                             const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, float4* node_out,
-                             unsigned long long* next_item, int sm_count, cudaStream_t st) {
-  switch (shape) {
-    case 0: return launch_deflect32_t<256, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    case 2: return launch_deflect32_t<128, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    case 3: return launch_deflect32_t<128, 8>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    default: return launch_deflect32_t<256, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                               n_items, node_out, next_item, sm_count, st);
-  }
-}
-
-__global__ void k_unpack32(const float4* __restrict__ nodes, int64_t n, float2* __restrict__ alpha,
-                           float* __restrict__ err) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float4 v = nodes[i];
-    alpha[i] = make_float2(v.x, v.y);
-    if (err) err[i] = v.z;
-  }
-}
-
-cudaError_t launch_unpack32(const float4* nodes, int64_t n, float2* alpha, float* err,
-                            cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > 65535 * 8) blocks = 65535 * 8;
-  k_unpack32<<<(unsigned)blocks, 256, 0, st>>>(nodes, n, alpha, err);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------- triangle search
 constexpr int kSearchThreads = 256;  // cells per work item (one per thread)
@@ -265,7 +109,26 @@ struct StripBox {
 // surviving sources of each strip are compacted into a shared list; (2) each
 // warp runs the per-cell test only for its strip's survivors.  Most pairs
 // never reach the per-cell arithmetic.
-__global__ void __launch_bounds__(kSearchThreads)
+// Image position of an FP32-certified hit, interpolated in FP64 from the
+// triangle's node coordinates: T0 = (X0,Y0), (X1,Y0), (X1,Y1); T1 = (X0,Y0),
+// (X1,Y1), (X0,Y1); w1, w2 the barycentric weights of the 2nd and 3rd
+// vertex.  Out of line so that the compiler does not hoist this rare FP64
+// work (GB300's FP64 pipe runs at 1/64 of the FP32 rate) into the per-cell
+// path.
+__device__ __noinline__ double2 hit_xy(double x0, double y0, double dx, double dy, int i, int j,
+                                       int t, float w1, float w2) {
+  const double X0 = x0 + (double)i * dx, X1 = x0 + (double)(i + 1) * dx;
+  const double Y0 = y0 + (double)j * dy, Y1 = y0 + (double)(j + 1) * dy;
+  if (t == 0)
+    return make_double2(X0 + (double)w1 * (X1 - X0) + (double)w2 * (X1 - X0),
+                        Y0 + (double)w2 * (Y1 - Y0));
+  return make_double2(X0 + (double)w1 * (X1 - X0),
+                      Y0 + (double)w1 * (Y1 - Y0) + (double)w2 * (Y1 - Y0));
+}
+
+// Three blocks per SM (80 registers, a few bytes of spill) measure faster
+// than two without spill: the kernel is latency-bound.
+__global__ void __launch_bounds__(kSearchThreads, 3)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
                Hit* __restrict__ hits, int64_t hit_cap, Work64* __restrict__ work,
@@ -403,23 +266,21 @@ __global__ void __launch_bounds__(kSearchThreads)
         const bool wk1 = r1 == 2 || (r1 == 1 && !ok1);
         if (__any_sync(0xffffffffu, ok0 || ok1 || wk0 || wk1)) {
           const int64_t tri0 = 2 * cl, tri1 = 2 * cl + 1;
-          const double X0 = g.x0 + (double)i * g.dx, X1 = g.x0 + (double)(i + 1) * g.dx;
-          const double Y0 = g.y0 + (double)j * g.dy, Y1 = g.y0 + (double)(j + 1) * g.dy;
           Hit h;
           h.src = s0 + k;
           h.fp64 = 0;
-          // T0 vertices: (X0,Y0), (X1,Y0), (X1,Y1)
           h.tri = tri0;
           h.w[0] = w0[0]; h.w[1] = w0[1]; h.w[2] = w0[2];
-          h.x = X0 + (double)w0[1] * (X1 - X0) + (double)w0[2] * (X1 - X0);
-          h.y = Y0 + (double)w0[2] * (Y1 - Y0);
+          double2 xy = hit_xy(g.x0, g.y0, g.dx, g.dy, i, j, 0, w0[1], w0[2]);
+          h.x = xy.x;
+          h.y = xy.y;
           Hit* hb = hits + (int64_t)b * hit_cap;
           warp_append_hit(ok0, h, hb, hit_cap, hit_count + b, status);
-          // T1 vertices: (X0,Y0), (X1,Y1), (X0,Y1)
           h.tri = tri1;
           h.w[0] = w1[0]; h.w[1] = w1[1]; h.w[2] = w1[2];
-          h.x = X0 + (double)w1[1] * (X1 - X0);
-          h.y = Y0 + (double)w1[1] * (Y1 - Y0) + (double)w1[2] * (Y1 - Y0);
+          xy = hit_xy(g.x0, g.y0, g.dx, g.dy, i, j, 1, w1[1], w1[2]);
+          h.x = xy.x;
+          h.y = xy.y;
           warp_append_hit(ok1, h, hb, hit_cap, hit_count + b, status);
           Work64* wb = work + (int64_t)b * work_cap;
           warp_append_work(wk0, Work64{sample, s0 + k, tri0, r0 == 2 ? 0 : 1, 0}, wb, work_cap,
@@ -462,93 +323,6 @@ cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const 
                                                           n_items, src, hits, hit_cap, work,
                                                           work_cap, hit_count, work_count,
                                                           counters, status, next_item);
-  return cudaGetLastError();
-}
-
-}  // namespace lt
-
-namespace lt {
-
-// ------------------------------------------------- the paper's mixed rule
-// Widen the FP32 deflections into the FP64 output and flag the nodes where
-// the distortion criteria fire (Eqs. 23-28): with d1 = a1(i,j) - a1(i-1,j),
-// d2 = a2(i,j) - a2(i,j-1), d3 = a1(i,j) - a1(i,j-1), d4 = a2(i,j) - a2(i-1,j),
-// recompute in FP64 if |h_x - d1| or |h_y - d2| < 0.0092" (h/0.03") or
-// |d3| or |d4| > 0.0104" (h/0.03"), h the node spacing along the difference.
-__global__ void k_paper_init(const float4* __restrict__ nodes, int nx, int ny, float hx, float hy,
-                             double2* __restrict__ out, unsigned char* __restrict__ flags) {
-  const int64_t n_all = (int64_t)nx * ny;
-  const float t12x = 0.0092f * hx / 0.03f, t12y = 0.0092f * hy / 0.03f;
-  const float t34x = 0.0104f * hx / 0.03f, t34y = 0.0104f * hy / 0.03f;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < n_all;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(n / nx), i = (int)(n - (int64_t)j * nx);
-    const float4 v = nodes[n];
-    out[n] = make_double2((double)v.x, (double)v.y);
-    bool crit = false;
-    if (i >= 1 && j >= 1) {
-      const float4 l = nodes[n - 1], b = nodes[n - nx];
-      const float d1 = v.x - l.x, d2 = v.y - b.y, d3 = v.x - b.x, d4 = v.y - l.y;
-      crit = fabsf(hx - d1) < t12x || fabsf(hy - d2) < t12y || fabsf(d3) > t34y ||
-             fabsf(d4) > t34x;
-    }
-    flags[n] = crit ? 1 : 0;
-  }
-}
-
-// Square patches centred on every halo: 2*half nodes on a side, half = 200
-// for cluster-scale halos (b0 >= LT_PAPER_CLUSTER_B0), 10 for the others
-// (App. A.3.2: 400 x 400 and 20 x 20 pixels).  One block per potential.
-__global__ void k_paper_patches(const Pot64* __restrict__ pot64, int n_pot, double x0, double y0,
-                                double dx, double dy, int nx, int ny,
-                                unsigned char* __restrict__ flags) {
-  const Pot64 p = pot64[blockIdx.x];
-  if (p.b0 <= 0.0) return;  // zero-mass or neutralised potential
-  const int half = p.b0 >= LT_PAPER_CLUSTER_B0 ? 200 : 10;
-  const long long ic = llround((p.cx - x0) / dx), jc = llround((p.cy - y0) / dy);
-  const int side = 2 * half;
-  for (int idx = threadIdx.x; idx < side * side; idx += blockDim.x) {
-    const long long i = ic - half + idx % side, j = jc - half + idx / side;
-    if (i >= 0 && i < nx && j >= 0 && j < ny) flags[j * (long long)nx + i] = 2;
-  }
-}
-
-// Compact the flagged nodes into a list (warp ballots, one atomic per warp).
-__global__ void k_paper_compact(const unsigned char* __restrict__ flags, int64_t n_all,
-                                int32_t* __restrict__ list, unsigned long long* count,
-                                float* __restrict__ map) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_all; base += stride) {
-    const int64_t n = base + threadIdx.x;
-    const bool f = n < n_all && flags[n] != 0;
-    if (map && n < n_all) map[n] = f ? 1.0f : 0.0f;
-    const unsigned mask = __ballot_sync(0xffffffffu, f);
-    if (!mask) continue;
-    const int leader = __ffs(mask) - 1;
-    unsigned long long b = 0;
-    if (lane == leader) b = atomicAdd(count, (unsigned long long)__popc(mask));
-    b = __shfl_sync(0xffffffffu, b, leader);
-    if (f) list[b + __popc(mask & ((1u << lane) - 1u))] = (int32_t)n;
-  }
-}
-
-cudaError_t launch_paper_flags(const float4* nodes, const Pot64* pot64, int n_pot,
-                               const lt_grid& g, double2* out, unsigned char* flags,
-                               int32_t* list, unsigned long long* count, float* map,
-                               int sm_count, cudaStream_t st) {
-  const int64_t n_all = (int64_t)g.nx * g.ny;
-  int64_t blocks = (n_all + 255) / 256;
-  if (blocks > (int64_t)sm_count * 32) blocks = (int64_t)sm_count * 32;
-  k_paper_init<<<(unsigned)blocks, 256, 0, st>>>(nodes, g.nx, g.ny, (float)g.dx, (float)g.dy,
-                                                 out, flags);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_paper_patches<<<n_pot, 256, 0, st>>>(pot64, n_pot, g.x0, g.y0, g.dx, g.dy, g.nx, g.ny,
-                                         flags);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-  k_paper_compact<<<(unsigned)blocks, 256, 0, st>>>(flags, n_all, list, count, map);
   return cudaGetLastError();
 }
 
