@@ -16,10 +16,10 @@
 //
 //   k_adj_hits / k_adj_bary  build those points and coefficients (vertex
 //                deflections of matched triangles recomputed in FP64);
-//   k_adj_grad   one thread per potential: the 2x6 Jacobian of its deflection
+//   k_adj_grad   one warp per potential: the 2x6 Jacobian of its deflection
 //                w.r.t. (x, y, e, phi, r_core, sigma_v) at every point, in
-//                FP32, contracted with the coefficients; FP32 partial sums of
-//                32 points are accumulated in FP64.
+//                FP32, contracted with the coefficients (one point per lane);
+//                FP32 warp sums of 32 points are accumulated in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -29,7 +29,6 @@
 namespace lt {
 
 constexpr int kAdjThreads = 128;
-constexpr int kAdjChunk = 256;
 
 // ------------------------------------------------------------ coefficients
 // Pass 1, one block per (sample, observed image m): if m is the first observed
@@ -38,14 +37,14 @@ constexpr int kAdjChunk = 256;
 // sums in index order): M = [beta_B - beta_A, beta_C - beta_A] is a
 // difference of large deflections and its FP32 rounding would be amplified
 // by M's conditioning in magnified triangles.
-constexpr int kAdjHitThreads = 128;
+constexpr int kAdjHitThreads = 384;  // one group of 128 per triangle vertex
 
 __global__ void __launch_bounds__(kAdjHitThreads)
     k_adj_hits(const Pot64* __restrict__ pot64, int n_pot, int batch,
                const SampleGrid* __restrict__ grids, const Hit* __restrict__ hits,
                int64_t hit_cap, lt_obs obs, const int32_t* __restrict__ match_hit,
                double2* __restrict__ lam, AdjPt* __restrict__ pts, int P) {
-  __shared__ double2 buf[3 * kAdjHitThreads];
+  __shared__ double2 buf[kAdjHitThreads];
   __shared__ double res[6];
   for (int64_t f = blockIdx.x; f < (int64_t)batch * obs.n_obs; f += gridDim.x) {
     const int b = (int)(f / obs.n_obs);
@@ -258,39 +257,36 @@ __device__ __forceinline__ void contract(const Pot64& P, float x, float y, float
   if (sv > 0.f) out[5] = 2.f / sv * (cpx * gx + cpy * gy);
 }
 
+// One warp per (sample, potential): lane l takes adjoint points l, l + 32, ...;
+// each round of 32 points is reduced across the warp in FP32 (a fixed
+// butterfly, so the result is deterministic) and accumulated in FP64.
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_grad(const Pot64* __restrict__ pot64, int n_pot, const AdjPt* __restrict__ pts, int P,
-               double* __restrict__ grad) {
-  __shared__ AdjPt sp[kAdjChunk];
-  const int b = blockIdx.y;
-  const int k = blockIdx.x * kAdjThreads + threadIdx.x;
-  const bool valid = k < n_pot;
-  const Pot64 p = pot64[(int64_t)b * n_pot + (valid ? k : 0)];
+    k_adj_grad(const Pot64* __restrict__ pot64, int n_pot, int batch,
+               const AdjPt* __restrict__ pts, int P, double* __restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * kAdjThreads + threadIdx.x) >> 5;
+  if (wid >= (int64_t)batch * n_pot) return;  // warp-uniform
+  const int b = (int)(wid / n_pot);
+  const Pot64 p = pot64[wid];
   const AdjPt* pb = pts + (int64_t)b * P;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int c0 = 0; c0 < P; c0 += kAdjChunk) {
-    const int cn = min(kAdjChunk, P - c0);
-    __syncthreads();
-    for (int v = threadIdx.x; v < cn; v += kAdjThreads) sp[v] = pb[c0 + v];
-    __syncthreads();
-    float part[6] = {0, 0, 0, 0, 0, 0};
-    for (int v = 0; v < cn; ++v) {
-      const AdjPt q = sp[v];
-      if (q.cx == 0.0 && q.cy == 0.0) continue;
-      float o[6];
-      contract(p, (float)q.x, (float)q.y, (float)q.cx, (float)q.cy, o);
-      for (int m = 0; m < 6; ++m) part[m] += o[m];
-      if ((v & 31) == 31) {
-        for (int m = 0; m < 6; ++m) {
-          acc[m] += part[m];
-          part[m] = 0.f;
-        }
-      }
+  for (int c0 = 0; c0 < P; c0 += 32) {
+    float o[6] = {0, 0, 0, 0, 0, 0};
+    const int v = c0 + lane;
+    if (v < P) {
+      const AdjPt q = pb[v];
+      if (q.cx != 0.0 || q.cy != 0.0)
+        contract(p, (float)q.x, (float)q.y, (float)q.cx, (float)q.cy, o);
     }
-    for (int m = 0; m < 6; ++m) acc[m] += part[m];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      float t = o[m];
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      acc[m] += t;
+    }
   }
-  if (valid)
-    for (int m = 0; m < 6; ++m) grad[((int64_t)b * n_pot + k) * 6 + m] = acc[m];
+  if (lane == 0)
+    for (int m = 0; m < 6; ++m) grad[wid * 6 + m] = acc[m];
 }
 
 cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const SampleGrid* grids,
@@ -308,8 +304,9 @@ cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const Sampl
   k_adj_bary<<<(unsigned)((warps + 127) / 128), 128, 0, st>>>(batch, obs, lam, pts, P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 grid((n_pot + kAdjThreads - 1) / kAdjThreads, batch);
-  k_adj_grad<<<grid, kAdjThreads, 0, st>>>(pot64, n_pot, pts, P, grad);
+  const int64_t gwarps = (int64_t)batch * n_pot;
+  const int64_t gblocks = (gwarps * 32 + kAdjThreads - 1) / kAdjThreads;
+  k_adj_grad<<<(unsigned)gblocks, kAdjThreads, 0, st>>>(pot64, n_pot, batch, pts, P, grad);
   return cudaGetLastError();
 }
 

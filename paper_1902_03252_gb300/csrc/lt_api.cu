@@ -79,6 +79,9 @@ struct lt_model {
   int64_t* d_match_tri = nullptr;
   int32_t* d_match_hit = nullptr;
   double* d_match_xy = nullptr;
+  // FP64 resolution scratch (node table, vertex slots, distinct-node list)
+  ResolveScratch rs{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  size_t rs_vslot_alloc = 0;
   double2* d_adj_lam = nullptr;   // adjoint: lambda per matched observed image
   AdjPt* d_adj_pts = nullptr;   // adjoint points (x, y, coefficient) [batch][4 n_obs]
   int obs_alloc = 0, sys_alloc = 0;
@@ -331,6 +334,36 @@ lt_status ensure_obs(lt_model* m, int n_obs, int n_sys) {
   return LT_OK;
 }
 
+// Scratch of the FP64 resolution for the largest chunk of the current plan.
+lt_status ensure_resolve(lt_model* m) {
+  int max_nb = 1;
+  for (const Chunk& c : m->plan.chunks) max_nb = std::max(max_nb, c.b1 - c.b0);
+  unsigned long long cap = 1024;
+  while (cap < 6ull * (unsigned long long)max_nb * (unsigned long long)m->work_cap) cap <<= 1;
+  LT_CHECK_ARG(cap <= (1ull << 31), "FP64 work capacity too large for one chunk");
+  const size_t vslots = (size_t)max_nb * m->work_cap * 3;
+  if (cap > m->rs.cap) {
+    ++m->ws_epoch;
+    if (m->rs.keys) LT_CUDA(cudaFree(m->rs.keys));
+    if (m->rs.hval) LT_CUDA(cudaFree(m->rs.hval));
+    if (m->rs.ulist) LT_CUDA(cudaFree(m->rs.ulist));
+    m->rs.keys = nullptr; m->rs.hval = nullptr; m->rs.ulist = nullptr; m->rs.cap = 0;
+    LT_CUDA(cudaMalloc(&m->rs.keys, sizeof(unsigned long long) * cap));
+    LT_CUDA(cudaMalloc(&m->rs.hval, sizeof(double2) * cap));
+    LT_CUDA(cudaMalloc(&m->rs.ulist, sizeof(int32_t) * cap));
+    m->rs.cap = cap;
+  }
+  if (!m->rs.n_unique) LT_CUDA(cudaMalloc(&m->rs.n_unique, sizeof(unsigned int)));
+  if (vslots > m->rs_vslot_alloc) {
+    ++m->ws_epoch;
+    if (m->rs.vslot) LT_CUDA(cudaFree(m->rs.vslot));
+    m->rs.vslot = nullptr;
+    LT_CUDA(cudaMalloc(&m->rs.vslot, sizeof(int32_t) * vslots));
+    m->rs_vslot_alloc = vslots;
+  }
+  return LT_OK;
+}
+
 // Prepare everything an enqueue needs (plan, workspaces) -- may allocate and
 // upload; must run outside stream capture.
 lt_status prepare(lt_model* m, const lt_grid* grids, int precision, int64_t hit_cap,
@@ -340,7 +373,9 @@ lt_status prepare(lt_model* m, const lt_grid* grids, int precision, int64_t hit_
   const size_t node_bytes = precision == LT_PREC_FP64 ? sizeof(double2) : sizeof(float4);
   s = ensure_nodes(m, m->plan.max_chunk_nodes * node_bytes);
   if (s != LT_OK) return s;
-  return ensure_lists(m, std::max(hit_cap, m->hit_cap), m->work_cap);
+  s = ensure_lists(m, std::max(hit_cap, m->hit_cap), m->work_cap);
+  if (s != LT_OK || precision == LT_PREC_FP64) return s;
+  return ensure_resolve(m);
 }
 
 // Deflection + search (+ FP64 resolution) of one chunk into the hit lists.
@@ -389,7 +424,7 @@ lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int
     }
     ProfScope ps(m, st, 2);
     LT_CUDA(launch_resolve64(m->d_pot64, m->n_pot, g, src, work, wc, nb, m->work_cap, hits,
-                             hit_cap, hc, m->d_counters, m->d_status, m->sm_count, st));
+                             hit_cap, hc, m->d_counters, m->d_status, m->rs, m->sm_count, st));
   }
   return LT_OK;
 }
@@ -530,7 +565,8 @@ void lt_model_destroy(lt_model* m) {
                   m->d_nodes, m->d_hits, m->d_work, m->d_hit_count, m->d_work_count,
                   m->d_plan_grids, m->d_plan_items, m->d_beta_obs, m->d_bary, m->d_match_tri,
                   m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched,
-                  m->d_src_beta, m->d_src_mu, m->d_src_bary};
+                  m->d_src_beta, m->d_src_mu, m->d_src_bary, m->rs.keys, m->rs.hval,
+                  m->rs.vslot, m->rs.ulist, m->rs.n_unique};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);

@@ -348,79 +348,187 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
 }
 
 
-constexpr int kResolveThreads = 128;
+// ------------------------------------------------------------ FP64 resolution
+// The FP64 work items of a chunk (ambiguous (triangle, source) pairs and hits
+// to refine) share many triangle nodes: the two triangles of a cell, and the
+// cells around a source that several systems' barycentres sit near.  Each
+// distinct node is evaluated in FP64 once:
+//   k_res_insert  one thread per (item, vertex): key (chunk-local sample,
+//                 node index) into an open-addressing table (linear probing,
+//                 capacity >= twice the number of vertices, so it cannot
+//                 fill); the thread that inserts a key appends its slot to
+//                 the list of distinct nodes;
+//   k_res_nodes   one block per distinct node: FP64 deflection summed in
+//                 potential index order (block_alpha64);
+//   k_res_tri     one thread per item: exact FP64 predicates with the tie
+//                 rule and the FP64 barycentric position.
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kResNodeThreads = 128;
 
-// One block per work item (items strided over blocks): the three vertex
-// deflections of the item's triangle in FP64 by the whole block, then the
-// exact predicate and interpolation by thread 0.
-__global__ void __launch_bounds__(kResolveThreads)
-    k_resolve64(const Pot64* __restrict__ pot64, int n_pot, const SampleGrid* __restrict__ grids,
-                Sources src, const Work64* __restrict__ work,
-                const unsigned long long* __restrict__ work_count, int n_samples, int64_t work_cap,
-                Hit* __restrict__ hits, int64_t hit_cap, unsigned long long* hit_count,
-                long long* counters, uint32_t* status) {
-  __shared__ double2 buf[3 * kResolveThreads];
-  __shared__ double res[6];
-  long long n_nodes = 0, n_hit = 0;
-  for (int64_t f = blockIdx.x; f < (int64_t)n_samples * work_cap; f += gridDim.x) {
+__device__ __forceinline__ unsigned long long res_hash(unsigned long long k) {
+  // splitmix64 finaliser
+  k ^= k >> 30;
+  k *= 0xbf58476d1ce4e5b9ull;
+  k ^= k >> 27;
+  k *= 0x94d049bb133111ebull;
+  k ^= k >> 31;
+  return k;
+}
+
+__device__ __forceinline__ void tri_vertex(const SampleGrid& g, int64_t tri, int v, int& i, int& j) {
+  const int64_t cell = tri / 2;
+  const int t = (int)(tri % 2);
+  i = (int)(cell % (g.nx - 1)) + (v == 0 ? 0 : (v == 1 ? 1 : (t == 0 ? 1 : 0)));
+  j = (int)(cell / (g.nx - 1)) + (v == 0 ? 0 : (v == 1 ? (t == 0 ? 0 : 1) : 1));
+}
+
+__global__ void k_res_insert(const Work64* __restrict__ work,
+                             const unsigned long long* __restrict__ work_count, int n_samples,
+                             int64_t work_cap, const SampleGrid* __restrict__ grids,
+                             unsigned long long* __restrict__ keys, unsigned long long mask,
+                             int32_t* __restrict__ vslot, int32_t* __restrict__ ulist,
+                             unsigned int* __restrict__ n_unique) {
+  const int64_t total = (int64_t)n_samples * work_cap * 3;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(f / (work_cap * 3));
+    const int64_t rem = f - (int64_t)b * work_cap * 3;
+    const int64_t idx = rem / 3;
+    const int v = (int)(rem - idx * 3);
+    const unsigned long long cnt = work_count[b];
+    if ((unsigned long long)idx >= (cnt < (unsigned long long)work_cap ? cnt : work_cap)) continue;
+    const Work64 wk = work[(int64_t)b * work_cap + idx];
+    const SampleGrid g = grids[b];
+    int i, j;
+    tri_vertex(g, wk.tri, v, i, j);
+    const unsigned long long key =
+        ((unsigned long long)b << 40) | (unsigned long long)((int64_t)j * g.nx + i);
+    unsigned long long h = res_hash(key) & mask;
+    int32_t slot = -1;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+      const unsigned long long prev = atomicCAS(&keys[h], kEmptyKey, key);
+      if (prev == kEmptyKey) {
+        ulist[atomicAdd(n_unique, 1u)] = (int32_t)h;
+        slot = (int32_t)h;
+        break;
+      }
+      if (prev == key) {
+        slot = (int32_t)h;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    vslot[((int64_t)b * work_cap + idx) * 3 + v] = slot;
+  }
+}
+
+__global__ void __launch_bounds__(kResNodeThreads)
+    k_res_nodes(const Pot64* __restrict__ pot64, int n_pot, int sample_base,
+                const SampleGrid* __restrict__ grids, const unsigned long long* __restrict__ keys,
+                const int32_t* __restrict__ ulist, const unsigned int* __restrict__ n_unique,
+                double2* __restrict__ hval, long long* counters) {
+  __shared__ double2 buf[kResNodeThreads];
+  __shared__ double res[2];
+  const unsigned int nu = *n_unique;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nu)
+    atomicAdd((unsigned long long*)&counters[CNT_FP64_NODES], (unsigned long long)nu);
+  for (unsigned int u = blockIdx.x; u < nu; u += gridDim.x) {
+    const int32_t slot = ulist[u];
+    const unsigned long long key = keys[slot];
+    const int b = (int)(key >> 40);
+    const int64_t node = (int64_t)(key & ((1ull << 40) - 1));
+    const SampleGrid g = grids[b];
+    const int j = (int)(node / g.nx), i = (int)(node - (int64_t)j * g.nx);
+    const double X = g.x0 + (double)i * g.dx;
+    const double Y = g.y0 + (double)j * g.dy;
+    block_alpha64<kResNodeThreads>(pot64 + (int64_t)(sample_base + b) * n_pot, n_pot, 1, &X, &Y,
+                                   &res[0], &res[1], buf);
+    if (threadIdx.x == 0) hval[slot] = make_double2(res[0], res[1]);
+  }
+}
+
+__global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
+                          const Work64* __restrict__ work,
+                          const unsigned long long* __restrict__ work_count, int n_samples,
+                          int64_t work_cap, const int32_t* __restrict__ vslot,
+                          const double2* __restrict__ hval, Hit* __restrict__ hits,
+                          int64_t hit_cap, unsigned long long* hit_count, long long* counters,
+                          uint32_t* status) {
+  long long n_hit = 0;
+  const int64_t total = (int64_t)n_samples * work_cap;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total;
+       f += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(f / work_cap);
     const int64_t idx = f - (int64_t)b * work_cap;
-    if ((unsigned long long)idx >= work_count[b]) continue;  // block-uniform
+    const unsigned long long cnt = work_count[b];
+    if ((unsigned long long)idx >= (cnt < (unsigned long long)work_cap ? cnt : work_cap)) continue;
     const Work64 wk = work[f];
     const SampleGrid g = grids[b];
-    const int64_t cell = wk.tri / 2;
-    const int t = (int)(wk.tri % 2);
-    const int i = (int)(cell % (g.nx - 1)), j = (int)(cell / (g.nx - 1));
-    // vertex (i, j) offsets of T0 = (00, 10, 11), T1 = (00, 11, 01)
-    const int di[3] = {0, 1, t == 0 ? 1 : 0};
-    const int dj[3] = {0, t == 0 ? 0 : 1, 1};
-    double X[3], Y[3];
+    const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
+    const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
+    const double Px = sxy[2 * wk.src], Py = sxy[2 * wk.src + 1];
+    double X[3], Y[3], Bx[3], By[3];
+    bool ok = true;
     for (int v = 0; v < 3; ++v) {
-      X[v] = g.x0 + (double)(i + di[v]) * g.dx;
-      Y[v] = g.y0 + (double)(j + dj[v]) * g.dy;
+      int i, j;
+      tri_vertex(g, wk.tri, v, i, j);
+      X[v] = g.x0 + (double)i * g.dx;
+      Y[v] = g.y0 + (double)j * g.dy;
+      const int32_t slot = vslot[f * 3 + v];
+      if (slot < 0) { ok = false; break; }
+      const double2 a = hval[slot];
+      Bx[v] = X[v] - r * a.x;
+      By[v] = Y[v] - r * a.y;
     }
-    block_alpha64<kResolveThreads>(pot64 + (int64_t)wk.sample * n_pot, n_pot, 3, X, Y, &res[0],
-                                   &res[3], buf);
-    n_nodes += 3;
-    if (threadIdx.x == 0) {
-      const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
-      const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
-      const double Px = sxy[2 * wk.src], Py = sxy[2 * wk.src + 1];
-      double Bx[3], By[3];
-      for (int v = 0; v < 3; ++v) {
-        Bx[v] = X[v] - r * res[v];
-        By[v] = Y[v] - r * res[3 + v];
-      }
-      double w[3];
-      if (in_tri64(Bx[0], By[0], Bx[1], By[1], Bx[2], By[2], Px, Py, w)) {
-        Hit h;
-        h.src = wk.src;
-        h.fp64 = 1;
-        h.tri = wk.tri;
-        h.w[0] = w[0]; h.w[1] = w[1]; h.w[2] = w[2];
-        h.x = w[0] * X[0] + w[1] * X[1] + w[2] * X[2];
-        h.y = w[0] * Y[0] + w[1] * Y[1] + w[2] * Y[2];
-        append_hit(h, hits + (int64_t)b * hit_cap, hit_cap, hit_count + b, status);
-        ++n_hit;
-      }
+    if (!ok) {  // cannot happen with the table sized as it is; recorded, never silent
+      atomicOr(status, ST_OVERFLOW_WORK);
+      continue;
     }
-    __syncthreads();
+    double w[3];
+    if (in_tri64(Bx[0], By[0], Bx[1], By[1], Bx[2], By[2], Px, Py, w)) {
+      Hit h;
+      h.src = wk.src;
+      h.fp64 = 1;
+      h.tri = wk.tri;
+      h.w[0] = w[0]; h.w[1] = w[1]; h.w[2] = w[2];
+      h.x = w[0] * X[0] + w[1] * X[1] + w[2] * X[2];
+      h.y = w[0] * Y[0] + w[1] * Y[1] + w[2] * Y[2];
+      append_hit(h, hits + (int64_t)b * hit_cap, hit_cap, hit_count + b, status);
+      ++n_hit;
+    }
   }
-  if (threadIdx.x == 0 && (n_nodes || n_hit)) {
-    atomicAdd((unsigned long long*)&counters[CNT_FP64_NODES], (unsigned long long)n_nodes);
+  for (int o = 16; o > 0; o >>= 1) n_hit += __shfl_xor_sync(0xffffffffu, n_hit, o);
+  if ((threadIdx.x & 31) == 0 && n_hit)
     atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
-  }
 }
 
 cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* grids, Sources src,
                              const Work64* work, const unsigned long long* work_count,
                              int n_samples, int64_t work_cap, Hit* hits, int64_t hit_cap,
                              unsigned long long* hit_count, long long* counters,
-                             uint32_t* status, int sm_count, cudaStream_t st) {
-  int blocks = sm_count * 8;
-  k_resolve64<<<blocks, kResolveThreads, 0, st>>>(pot64, n_pot, grids, src, work,
-                                                        work_count, n_samples, work_cap, hits,
-                                                        hit_cap, hit_count, counters, status);
+                             uint32_t* status, ResolveScratch rs, int sm_count,
+                             cudaStream_t st) {
+  // table capacity: the smallest power of two >= 2 x the vertex slots
+  unsigned long long cap = 1024;
+  while (cap < 6ull * (unsigned long long)n_samples * (unsigned long long)work_cap) cap <<= 1;
+  if (cap > rs.cap) return cudaErrorInvalidValue;  // sized by the caller from the same formula
+  cudaError_t e = cudaMemsetAsync(rs.keys, 0xff, sizeof(unsigned long long) * cap, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(rs.n_unique, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  const int64_t slots3 = (int64_t)n_samples * work_cap * 3;
+  int64_t b1 = (slots3 + 255) / 256;
+  if (b1 > (int64_t)sm_count * 16) b1 = (int64_t)sm_count * 16;
+  k_res_insert<<<(unsigned)b1, 256, 0, st>>>(work, work_count, n_samples, work_cap, grids,
+                                              rs.keys, cap - 1, rs.vslot, rs.ulist, rs.n_unique);
+  k_res_nodes<<<sm_count * 8, kResNodeThreads, 0, st>>>(pot64, n_pot, src.sample_base, grids,
+                                                         rs.keys, rs.ulist, rs.n_unique, rs.hval,
+                                                         counters);
+  int64_t b3 = ((int64_t)n_samples * work_cap + 127) / 128;
+  if (b3 > (int64_t)sm_count * 16) b3 = (int64_t)sm_count * 16;
+  k_res_tri<<<(unsigned)b3, 128, 0, st>>>(grids, src, work, work_count, n_samples, work_cap,
+                                           rs.vslot, rs.hval, hits, hit_cap, hit_count, counters,
+                                           status);
   return cudaGetLastError();
 }
 

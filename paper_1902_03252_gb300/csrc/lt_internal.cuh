@@ -128,33 +128,35 @@ __device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, 
 }
 
 // ------------------------------------------------- FP64 point deflections
-// Deflection at up to 3 points by a whole block of NT threads: thread t evaluates (point q,
-// potential c0 + t) for every point of a chunk of NT potentials, then thread
-// q sums point q's chunk in index order.  GB300's FP64 unit issues a warp
-// instruction only every few dozen cycles per SM sub-partition, so spreading
-// one evaluation over all four sub-partitions of an SM matters.  Must be
-// called by every thread of the block; results in ax[q], ay[q] (shared).
+// Deflection at up to 3 points by a whole block of NT threads.  The threads
+// form one group of NT/npts per point; in each chunk of NT/npts potentials,
+// thread k of group q evaluates (point q, potential c0 + k), and then thread
+// q sums its point's chunk in potential index order, so the result is the
+// oracle's left-to-right sum exactly.  GB300's FP64 unit issues a warp
+// instruction only every few dozen cycles per SM sub-partition, so giving each
+// thread a single evaluation (NT >= npts * n_pot) keeps the serial FP64 depth
+// of a block at one potential.  Must be called by every thread of the block;
+// results in ax[q], ay[q] (shared); buf holds NT double2.
 template <int NT>
 __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts,
                                      const double* px, const double* py, double* ax, double* ay,
-                                     double2* buf /*[3][NT]*/) {
+                                     double2* buf /*[NT]*/) {
   const int t = threadIdx.x;
+  const int G = NT / npts;
+  const int q = t / G, k = t - q * G;
   double sx = 0.0, sy = 0.0;
-  for (int c0 = 0; c0 < n_pot; c0 += NT) {
-    const int k = c0 + t;
-    if (k < n_pot) {
-      const Pot64 p = pb[k];
-      for (int q = 0; q < npts; ++q) {
-        double kx, ky;
-        alpha64_one(p, px[q], py[q], kx, ky);
-        buf[q * NT + t] = make_double2(kx, ky);
-      }
+  for (int c0 = 0; c0 < n_pot; c0 += G) {
+    if (q < npts && c0 + k < n_pot) {
+      const Pot64 p = pb[c0 + k];
+      double kx, ky;
+      alpha64_one(p, px[q], py[q], kx, ky);
+      buf[q * G + k] = make_double2(kx, ky);
     }
     __syncthreads();
     if (t < npts) {
-      const int cn = min(NT, n_pot - c0);
+      const int cn = min(G, n_pot - c0);
       for (int m = 0; m < cn; ++m) {
-        const double2 v = buf[t * NT + m];
+        const double2 v = buf[t * G + m];
         sx = sx + v.x;
         sy = sy + v.y;
       }
@@ -305,11 +307,24 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
                             int n_samples, int64_t n_items, Sources src, Hit* hits,
                             int64_t hit_cap, unsigned long long* hit_count, long long* counters,
                             uint32_t* status, int sm_count, cudaStream_t st);
+// Scratch of the FP64 resolution: node table (keys, values), per-vertex slots,
+// list of distinct nodes and its length.  cap: table entries (power of two)
+// allocated, at least the smallest power of two >= 6 x samples x work_cap of
+// any chunk.
+struct ResolveScratch {
+  unsigned long long* keys;
+  double2* hval;
+  int32_t* vslot;  // [samples][work_cap][3]
+  int32_t* ulist;  // [cap]
+  unsigned int* n_unique;
+  unsigned long long cap;
+};
 cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* grids, Sources src,
                              const Work64* work, const unsigned long long* work_count,
                              int n_samples, int64_t work_cap, Hit* hits, int64_t hit_cap,
                              unsigned long long* hit_count, long long* counters,
-                             uint32_t* status, int sm_count, cudaStream_t st);
+                             uint32_t* status, ResolveScratch rs, int sm_count,
+                             cudaStream_t st);
 cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_count, int n_samples,
                              int64_t hit_cap, int sample_base, lt_image* out, int64_t out_cap,
                              int64_t* n_out, uint32_t* status, cudaStream_t st);
