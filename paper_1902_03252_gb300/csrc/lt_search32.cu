@@ -72,7 +72,7 @@ __device__ __forceinline__ void warp_append_hit(bool flag, const Hit& h, Hit* hi
 
 __device__ __forceinline__ void warp_append_work(bool flag, const Work64& wk, Work64* work,
                                                  int64_t cap, unsigned long long* count,
-                                                 uint32_t* status) {
+                                                 uint32_t* status, long long* counters) {
   unsigned mask = __ballot_sync(0xffffffffu, flag);
   if (!mask) return;
   int lane = threadIdx.x & 31;
@@ -82,8 +82,12 @@ __device__ __forceinline__ void warp_append_work(bool flag, const Work64& wk, Wo
   base = __shfl_sync(0xffffffffu, base, leader);
   if (flag) {
     unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
-    if (idx < (unsigned long long)cap) work[idx] = wk;
-    else atomicOr(status, ST_OVERFLOW_WORK);
+    if (idx < (unsigned long long)cap) {
+      work[idx] = wk;
+    } else {  // dropped: latched and counted
+      atomicOr(status, ST_OVERFLOW_WORK);
+      atomicAdd((unsigned long long*)&counters[CNT_DROPPED], 1ull);
+    }
   }
 }
 
@@ -284,9 +288,9 @@ __global__ void __launch_bounds__(kSearchThreads, 3)
           warp_append_hit(ok1, h, hb, hit_cap, hit_count + b, status);
           Work64* wb = work + (int64_t)b * work_cap;
           warp_append_work(wk0, Work64{sample, s0 + k, tri0, r0 == 2 ? 0 : 1, 0}, wb, work_cap,
-                           work_count + b, status);
+                           work_count + b, status, counters);
           warp_append_work(wk1, Work64{sample, s0 + k, tri1, r1 == 2 ? 0 : 1, 0}, wb, work_cap,
-                           work_count + b, status);
+                           work_count + b, status, counters);
           n_hit += (int)ok0 + (int)ok1;
           n_amb += (int)(r0 == 2) + (int)(r1 == 2);
           n_ref += (int)(r0 == 1 && !ok0) + (int)(r1 == 1 && !ok1);

@@ -154,3 +154,18 @@ def test_c5_full_size_local_checks(oracle):
             fd = (oracle.chi2_frozen(pp, grid, o, mt) - oracle.chi2_frozen(pm, grid, o, mt)) / (2 * h)
             floor = 1e-6 * np.abs(g).max()
             assert abs(g[k, c] - fd) <= 1e-3 * abs(fd) + floor, (k, c, g[k, c], fd)
+
+
+def test_c5_work_overflow_is_reported():
+    """A c5 sample has ~16k ambiguous (triangle, source) pairs: with the
+    default per-sample capacity of 4096 the FP64 work list overflows, which
+    sync reports as LT_ERR_OVERFLOW with the dropped count, never silently."""
+    w = W.c5(batch=1)
+    o = load_obs("c5")
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    m.chi2([w.grids[0].as_tuple()], lt.Observations.from_dict(o), precision=lt.MIXED)
+    st, stats = m.sync()
+    assert st == lt.LT_ERR_OVERFLOW
+    assert stats["work_overflow"] > 0
+    m.close()
