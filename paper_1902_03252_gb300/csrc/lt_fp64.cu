@@ -646,12 +646,24 @@ cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_coun
 // reduced by warp shuffles in a fixed order, then across warps.
 constexpr int kChi2Threads = 128;
 
+// The hit list is staged through shared memory in chunks (each thread's scan
+// over the hits would otherwise be a chain of dependent global-memory
+// latencies); each thread keeps its observed image's best match so far.
+constexpr int kChi2Stage = 512;
+
+struct HitXY {
+  double x, y;
+  int64_t tri;
+  int32_t src, pad;
+};
+
 __global__ void __launch_bounds__(kChi2Threads)
     k_chi2(const Hit* __restrict__ hits, const unsigned long long* __restrict__ hit_count,
            int64_t hit_cap, int sample_base, const SampleGrid* __restrict__ grids, lt_obs obs,
            double* __restrict__ chi2, int64_t* __restrict__ match_tri,
            int32_t* __restrict__ match_hit, double* __restrict__ match_xy) {
   __shared__ double wsum[kChi2Threads / 32];
+  __shared__ HitXY sh[kChi2Stage];
   const int b = blockIdx.x;
   const int sample = sample_base + b;
   const SampleGrid g = grids[b];
@@ -660,35 +672,50 @@ __global__ void __launch_bounds__(kChi2Threads)
   const double Lx = (g.nx - 1) * g.dx, Ly = (g.ny - 1) * g.dy;
   const double diag = sqrt(Lx * Lx + Ly * Ly);
   double acc = 0.0;
-  for (int m = threadIdx.x; m < obs.n_obs; m += kChi2Threads) {
-    const int i = obs.sys[m];
-    const double ox = obs.x[m], oy = obs.y[m], sg = obs.sigma[m];
-    int64_t best = -1;
+  for (int m0 = 0; m0 < obs.n_obs; m0 += kChi2Threads) {
+    const int m = m0 + threadIdx.x;
+    const bool act = m < obs.n_obs;
+    const int i = act ? obs.sys[m] : -1;
+    const double ox = act ? obs.x[m] : 0.0, oy = act ? obs.y[m] : 0.0;
+    int64_t best = -1, best_tri = 0;
     double bd = 0.0;
-    for (int64_t h = 0; h < n; ++h) {
-      if (hb[h].src != i) continue;
-      const double ex = ox - hb[h].x, ey = oy - hb[h].y;
-      const double d2 = ex * ex + ey * ey;
-      if (best < 0 || d2 < bd || (d2 == bd && hb[h].tri < hb[best].tri)) {
-        best = h;
-        bd = d2;
+    for (int64_t h0 = 0; h0 < n; h0 += kChi2Stage) {
+      const int cn = (int)min((int64_t)kChi2Stage, n - h0);
+      __syncthreads();
+      for (int v = threadIdx.x; v < cn; v += kChi2Threads) {
+        const Hit& H = hb[h0 + v];
+        sh[v] = HitXY{H.x, H.y, H.tri, H.src, 0};
+      }
+      __syncthreads();
+      for (int v = 0; v < cn; ++v) {
+        if (sh[v].src != i) continue;
+        const double ex = ox - sh[v].x, ey = oy - sh[v].y;
+        const double d2 = ex * ex + ey * ey;
+        if (best < 0 || d2 < bd || (d2 == bd && sh[v].tri < best_tri)) {
+          best = h0 + v;
+          best_tri = sh[v].tri;
+          bd = d2;
+        }
       }
     }
-    double term;
-    const int64_t o = (int64_t)sample * obs.n_obs + m;
-    if (best < 0) {
-      const double t = diag / sg;
-      term = t * t;
-      if (match_tri) match_tri[o] = -1;
-      if (match_hit) match_hit[o] = -1;
-      if (match_xy) { match_xy[2 * o] = 0.0; match_xy[2 * o + 1] = 0.0; }
-    } else {
-      term = bd / (sg * sg);
-      if (match_tri) match_tri[o] = hb[best].tri;
-      if (match_hit) match_hit[o] = (int32_t)best;
-      if (match_xy) { match_xy[2 * o] = hb[best].x; match_xy[2 * o + 1] = hb[best].y; }
+    if (act) {
+      const double sg = obs.sigma[m];
+      double term;
+      const int64_t o = (int64_t)sample * obs.n_obs + m;
+      if (best < 0) {
+        const double t = diag / sg;
+        term = t * t;
+        if (match_tri) match_tri[o] = -1;
+        if (match_hit) match_hit[o] = -1;
+        if (match_xy) { match_xy[2 * o] = 0.0; match_xy[2 * o + 1] = 0.0; }
+      } else {
+        term = bd / (sg * sg);
+        if (match_tri) match_tri[o] = hb[best].tri;
+        if (match_hit) match_hit[o] = (int32_t)best;
+        if (match_xy) { match_xy[2 * o] = hb[best].x; match_xy[2 * o + 1] = hb[best].y; }
+      }
+      acc = acc + term;
     }
-    acc = acc + term;
   }
   for (int off = 16; off > 0; off >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
