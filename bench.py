@@ -137,12 +137,24 @@ def measured_peaks():
         return {}
 
 
+def _code_only(name: str, text: str) -> str:
+    """The code of a source file without its comments and blank lines, so that
+    an edit to a comment does not change the key of a kernel's profile."""
+    if name.endswith(".py"):
+        text = re.sub(r"#[^\n]*", "", text)
+    else:
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+    lines = (" ".join(ln.split()) for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def source_sha(files) -> str:
-    """sha256 over the concatenated kernel sources (csrc/ file names)."""
+    """sha256 over the code of the kernel sources (csrc/ file names)."""
     h = hashlib.sha256()
     for name in files:
-        with open(os.path.join(ROOT, "paper_1902_03252_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1902_03252_gb300", "csrc", name)) as f:
+            h.update(_code_only(name, f.read()).encode())
     return h.hexdigest()
 
 

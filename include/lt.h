@@ -227,9 +227,9 @@ lt_status lt_chi2_graph(lt_model* model, const lt_grid* grids, const lt_obs* obs
 
 /* Choose the launch shape of the FP32 deflection kernel by index, in
  * [0, lt_num_shapes()): (threads per block, nodes per thread) of
- * (256, 2), (256, 4), (128, 4), (128, 8).  Every shape computes the same
- * quantities within the same error bound; only speed differs.  lt_autotune
- * picks one by timing.  Errors: LT_ERR_INVALID_ARG. */
+ * (256, 4) (the default), (256, 2), (512, 2), (128, 4), (128, 8).  Every
+ * shape computes the same values; only speed differs.  lt_autotune picks one
+ * by timing.  Errors: LT_ERR_INVALID_ARG. */
 lt_status lt_model_set_shape(lt_model* model, int32_t shape);
 int32_t lt_num_shapes(void);
 

@@ -45,7 +45,7 @@ struct lt_model {
   int n_pot = 0, batch = 0;
   int64_t hit_cap = kDefaultCap, work_cap = kDefaultCap;
   int device = 0, sm_count = 1;
-  int shape = 1;  // FP32 deflection launch shape (autotuned)
+  int shape = 0;  // FP32 deflection launch shape (autotuned)
   size_t ws_budget = (size_t)4 << 30;
   double* d_params = nullptr;
   Pot64* d_pot64 = nullptr;

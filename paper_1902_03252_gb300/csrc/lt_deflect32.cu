@@ -79,9 +79,7 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
       }
       for (int k = e_sis; k < e_pie; ++k) {
         const float4* f = &sp[k * 5];
-        const float P = f[4].x;
-#pragma unroll
-        for (int m = 0; m < NPT; ++m) piemd32(f, P, X[m], Y[m], AX[m], AY[m], ER[m]);
+        piemd32_nodes<NPT>(f, f[4].x, X, Y, AX, AY, ER);
       }
       for (int k = e_pie; k < cn; ++k) {
         const float4* f = &sp[k * 5];
@@ -124,11 +122,13 @@ cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
                              int64_t n_items, int shape, float4* node_out,
                              unsigned long long* next_item, int sm_count, cudaStream_t st) {
   switch (shape) {
-    case 0: return launch_deflect32_t<256, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
+    case 1: return launch_deflect32_t<256, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
                                               n_items, node_out, next_item, sm_count, st);
-    case 2: return launch_deflect32_t<128, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
+    case 2: return launch_deflect32_t<512, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
                                               n_items, node_out, next_item, sm_count, st);
-    case 3: return launch_deflect32_t<128, 8>(pot32, seg, n_pot, grids, item_off, n_samples,
+    case 3: return launch_deflect32_t<128, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
+                                              n_items, node_out, next_item, sm_count, st);
+    case 4: return launch_deflect32_t<128, 8>(pot32, seg, n_pot, grids, item_off, n_samples,
                                               n_items, node_out, next_item, sm_count, st);
     default: return launch_deflect32_t<256, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
                                                n_items, node_out, next_item, sm_count, st);

@@ -223,10 +223,10 @@ struct DeflectShape {
   int threads;  // threads per block
   int npt;      // nodes per thread
 };
-constexpr int kNumShapes = 4;
+constexpr int kNumShapes = 5;
 __host__ __device__ inline DeflectShape deflect_shape(int v) {
-  const DeflectShape tab[kNumShapes] = {{256, 2}, {256, 4}, {128, 4}, {128, 8}};
-  return tab[v < 0 || v >= kNumShapes ? 1 : v];
+  const DeflectShape tab[kNumShapes] = {{256, 4}, {256, 2}, {512, 2}, {128, 4}, {128, 8}};
+  return tab[v < 0 || v >= kNumShapes ? 0 : v];
 }
 
 // ----------------------------------------------------------- batch layout

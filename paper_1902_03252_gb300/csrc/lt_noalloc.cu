@@ -108,8 +108,7 @@ __global__ void __launch_bounds__(kNT)
       }
       for (int k = e_sis; k < e_pie; ++k) {
 #pragma unroll
-        for (int m = 0; m < kNPT; ++m)
-          piemd32(&sp[k * 5], sp[k * 5 + 4].x, X[m], Y[m], AX[m], AY[m], ER[m]);
+        piemd32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
       }
       for (int k = e_pie; k < cn; ++k) {
 #pragma unroll

@@ -92,7 +92,7 @@ def test_deflect_mixed_within_running_bound(oracle, seed):
     assert ratio.max() <= 1.0
 
 
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", range(5))
 def test_deflect_every_shape_within_bound(oracle, shape):
     """Every launch shape of the FP32 deflection on 300 potentials of all
     three kinds -- more than one staged chunk of 256 -- over a grid whose node
@@ -108,7 +108,7 @@ def test_deflect_every_shape_within_bound(oracle, shape):
     m.set_params(p[None])
     m.set_shape(shape)
     a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
-    m.set_shape(1)
+    m.set_shape(0)
     a1, e1 = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
     assert m.sync()[0] == lt.LT_OK
     a, e = a.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
