@@ -279,6 +279,7 @@ def run_ours(a, rank, world, local):
     obs = lt.Observations.from_dict(o, device=dev)
     shape = None if a.no_autotune else m.autotune(grid[0])
     out = torch.empty(1, dtype=torch.float64, device=dev)
+    dev_params = torch.as_tensor(np.ascontiguousarray(w.params), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     # correctness of the timed configuration
@@ -289,6 +290,7 @@ def run_ours(a, rank, world, local):
 
     def timed(precision, steps, warmup):
         for _ in range(warmup):
+            m.set_params(dev_params)
             m.chi2(grid, obs, precision=precision, out=out)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -301,6 +303,9 @@ def run_ours(a, rank, world, local):
         for k in range(steps):
             flush.zero_()
             ev[k][0].record()
+            # one step = the whole path for one proposal: parameter preparation
+            # from the device-resident parameters, then the chi^2 evaluation
+            m.set_params(dev_params)
             m.chi2(grid, obs, precision=precision, out=out)
             ev[k][1].record()
         torch.cuda.synchronize()
@@ -357,8 +362,6 @@ def run_ours(a, rank, world, local):
     d64 = prof64["deflect"]
     defl64_ms = d64["ms"] / max(1, d64["launches"])
     launches_per_step = sum(prof[k]["launches"] for k in prof) / a.steps
-    # k_bary_obs and k_bary_sys share one timing bracket: count both
-    launches_per_step += 1
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -367,6 +370,7 @@ def run_ours(a, rank, world, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "mixed",
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
+                   "step": "parameter preparation from device-resident parameters + chi^2",
                    "deflect_shape": shape},
         "node_pot_per_s": value * node_pot,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64,
@@ -385,7 +389,8 @@ def run_ours(a, rank, world, local):
                 "h2d_bytes_per_step": int(host_params.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8), "ms_per_step": e2e_ms},
         "clocks": clk,
-        "gpu_launches": int(round(launches_per_step * a.steps)),
+        # kernels of the chi^2 stages (counted by the library) + k_prep per step
+        "gpu_launches": int(round((launches_per_step + 1) * a.steps)),
         "wall_s_timed_region": wall,
         "deflect32_source_sha256": source_sha(DEFLECT32_SOURCES),
     }

@@ -245,9 +245,11 @@ lt_status lt_autotune(lt_model* model, const lt_grid* grid, uintptr_t stream, in
  * on the caller's stream (not inside lt_chi2_graph).  lt_profile_read waits
  * for the recorded events and returns the totals since the last reset. */
 typedef struct {
-  int64_t launches[4]; /* [0] deflection, [1] search, [2] FP64 resolution,
-                          [3] barycentres + chi^2 */
-  double ms[4];        /* summed event durations of those launches */
+  int64_t launches[4]; /* kernel launches of [0] the deflection, [1] the
+                          search, [2] the FP64 resolution (3 kernels per
+                          chunk), [3] barycentres (2) + chi^2 (1) */
+  double ms[4];        /* summed event durations of those stages (one event
+                          pair per stage and chunk) */
   double node_pot[2];  /* node x potential evaluations by the deflection
                           launches: [0] FP32, [1] FP64 */
 } lt_profile;

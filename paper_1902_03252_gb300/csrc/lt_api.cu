@@ -107,6 +107,7 @@ struct lt_model {
     cudaEvent_t e0, e1;
     double node_pot;
     int fp64;
+    int kernels;  // kernel launches inside the timed scope
   };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
@@ -143,9 +144,11 @@ struct ProfScope {
   int kind;
   double node_pot;
   int fp64;
+  int kernels;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  ProfScope(lt_model* m_, cudaStream_t st_, int kind_, double np = 0.0, int fp64_ = 0)
-      : m(m_), st(st_), kind(kind_), node_pot(np), fp64(fp64_) {
+  ProfScope(lt_model* m_, cudaStream_t st_, int kind_, double np = 0.0, int fp64_ = 0,
+            int kernels_ = 1)
+      : m(m_), st(st_), kind(kind_), node_pot(np), fp64(fp64_), kernels(kernels_) {
     if (!m->prof_on) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
@@ -166,7 +169,7 @@ struct ProfScope {
   ~ProfScope() {
     if (!e0 || !e1) return;
     cudaEventRecord(e1, st);
-    m->prof_pending.push_back({kind, e0, e1, node_pot, fp64});
+    m->prof_pending.push_back({kind, e0, e1, node_pot, fp64, kernels});
   }
 };
 
@@ -422,7 +425,7 @@ lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int
                               m->work_cap, hc, wc, m->d_counters, m->d_status, next_search,
                               m->sm_count, st));
     }
-    ProfScope ps(m, st, 2);
+    ProfScope ps(m, st, 2, 0.0, 0, 3);  // k_res_insert, k_res_nodes, k_res_tri
     LT_CUDA(launch_resolve64(m->d_pot64, m->n_pot, g, src, work, wc, nb, m->work_cap, hits,
                              hit_cap, hc, m->d_counters, m->d_status, m->rs, m->sm_count, st));
   }
@@ -457,7 +460,7 @@ lt_status enqueue_chi2(lt_model* m, const lt_obs& obs, int precision, double* ch
   LT_CUDA(cudaEventRecord(m->ev_fork, st));
   LT_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
   {
-    ProfScope ps(m, m->side, 3);
+    ProfScope ps(m, m->side, 3, 0.0, 0, 2);  // k_bary_obs, k_bary_sys
     LT_CUDA(launch_barycentres(m->d_pot64, m->n_pot, m->batch, obs, m->d_beta_obs, m->d_bary,
                                m->side));
   }
@@ -877,7 +880,7 @@ lt_status lt_profile_read(lt_model* m, lt_profile* out, int reset) {
     LT_CUDA(cudaEventSynchronize(r.e1));
     float ms = 0.f;
     LT_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
-    m->prof_acc.launches[r.kind] += 1;
+    m->prof_acc.launches[r.kind] += r.kernels;
     m->prof_acc.ms[r.kind] += ms;
     if (r.kind == 0) m->prof_acc.node_pot[r.fp64] += r.node_pot;
     m->prof_pool.push_back(r.e0);

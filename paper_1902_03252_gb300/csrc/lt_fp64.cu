@@ -45,16 +45,20 @@ __device__ __forceinline__ bool valid_params(const double* v, int* kind_out) {
 
 // One block per sample.  Pass 1 validates every potential and writes its
 // FP64 record (invalid ones are latched and neutralised to a zero-mass SIS);
-// pass 2 ranks potentials kind-major in index order and writes the FP32
-// record at that rank, so the FP32 kernel loops over kind segments.
+// pass 2 ranks potentials kind-major in index order (block-wide ballot
+// prefix counts) and writes the FP32 record at that rank, so the FP32 kernel
+// loops over kind segments.
 __global__ void __launch_bounds__(kPrepThreads)
     k_prep(const double* __restrict__ params, int n_pot, Pot64* __restrict__ pot64,
            Pot32* __restrict__ pot32, Seg32* __restrict__ seg, uint32_t* status) {
+  constexpr int NW = kPrepThreads / 32;
   const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double* P = params + (int64_t)b * LT_N_ROWS * n_pot;
   Pot64* p64 = pot64 + (int64_t)b * n_pot;
   __shared__ int cnt[3];
-  __shared__ float qpart[kPrepThreads];
+  __shared__ int wcnt[3][NW];
+  __shared__ float qpart[NW];
   if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < n_pot; k += kPrepThreads) {
@@ -69,8 +73,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     p.kind = (double)kind;
     p.cx = v[LT_ROW_X];
     p.cy = v[LT_ROW_Y];
-    p.c = cos(v[LT_ROW_PHI]);
-    p.s = sin(v[LT_ROW_PHI]);
+    sincos(v[LT_ROW_PHI], &p.s, &p.c);
     double t = v[LT_ROW_SIGMA] / kC;
     p.b0 = 4.0 * kPi * t * t * kArcsec;
     p.e = v[LT_ROW_E];
@@ -87,14 +90,34 @@ __global__ void __launch_bounds__(kPrepThreads)
   }
   __syncthreads();
   float qsum = 0.0f;
-  for (int k = threadIdx.x; k < n_pot; k += kPrepThreads) {
-    const Pot64 p = p64[k];
-    const int kind = (int)p.kind;
-    int rank = 0;
-    for (int m = 0; m < n_pot; ++m) {
-      const int km = (int)p64[m].kind;
-      if (km < kind || (km == kind && m < k)) ++rank;
+  int base[3] = {0, 0, 0};  // potentials of each kind in earlier chunks
+  for (int k0 = 0; k0 < n_pot; k0 += kPrepThreads) {
+    const int k = k0 + threadIdx.x;
+    const bool act = k < n_pot;
+    Pot64 p;
+    int kind = -1;
+    if (act) {
+      p = p64[k];
+      kind = (int)p.kind;
     }
+    // rank = potentials of a lower kind + potentials of this kind before k
+    int before = 0;
+    for (int j = 0; j < 3; ++j) {
+      const unsigned m = __ballot_sync(0xffffffffu, kind == j);
+      if (lane == 0) wcnt[j][wid] = __popc(m);
+      if (kind == j) before = __popc(m & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    int rank = 0;
+    if (act) {
+      for (int j = 0; j < kind; ++j) rank += cnt[j];
+      rank += base[kind] + before;
+      for (int w = 0; w < wid; ++w) rank += wcnt[kind][w];
+    }
+    for (int j = 0; j < 3; ++j)
+      for (int w = 0; w < NW; ++w) base[j] += wcnt[j][w];
+    __syncthreads();
+    if (!act) continue;
     Pot32 f;
     for (int w = 0; w < 5; ++w) f.f[w] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float cx = (float)p.cx, cy = (float)p.cy, c = (float)p.c, s = (float)p.s;
@@ -133,11 +156,13 @@ __global__ void __launch_bounds__(kPrepThreads)
     qsum += (float)Q;
     pot32[(int64_t)b * n_pot + rank] = f;
   }
-  qpart[threadIdx.x] = qsum;
+  // sum of the static bound terms: fixed order (warp butterflies, then warps)
+  for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, o);
+  if (lane == 0) qpart[wid] = qsum;
   __syncthreads();
   if (threadIdx.x == 0) {
     float tot = 0.0f;
-    for (int t = 0; t < kPrepThreads; ++t) tot += qpart[t];
+    for (int w = 0; w < NW; ++w) tot += qpart[w];
     seg[b] = Seg32{cnt[LT_SIS], cnt[LT_PIEMD], cnt[LT_SIE], tot};
   }
 }

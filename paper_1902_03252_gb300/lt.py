@@ -61,7 +61,7 @@ class Profile(C.Structure):
                 ("node_pot", C.c_double * 2)]
 
 
-PROFILE_KINDS = ("deflect", "search", "resolve64", "chi2")
+PROFILE_KINDS = ("deflect", "search", "resolve", "bary_chi2")
 
 IMAGE_DTYPE = np.dtype([("sample", "<i4"), ("src", "<i4"), ("tri", "<i8"), ("x", "<f8"),
                         ("y", "<f8"), ("w", "<f8", (3,)), ("fp64", "<i4"), ("reserved", "<i4")])
