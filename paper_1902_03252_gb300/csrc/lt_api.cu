@@ -21,7 +21,7 @@ namespace {
 
 constexpr int64_t kDefaultCap = 4096;
 constexpr int kDefl64Nodes = 128;    // nodes per FP64 deflection item
-constexpr int kSearch32Cells = 256;  // cells per FP32 search item
+constexpr int kSearch32Cells = 128;  // cells per FP32 search item (= k_search32 block size)
 constexpr int kSearch64Cells = 128;  // cells per FP64 search item
 
 struct Chunk {

@@ -11,7 +11,7 @@
 namespace lt {
 
 // ---------------------------------------------------------- triangle search
-constexpr int kSearchThreads = 256;  // cells per work item (one per thread)
+constexpr int kSearchThreads = 128;  // cells per work item (one per thread)
 constexpr int kMaxSrcSmem = 256;     // sources staged in shared memory at a time
 
 // Source data staged per sample: position relative coordinates use FP32.
@@ -130,9 +130,11 @@ __device__ __noinline__ double2 hit_xy(double x0, double y0, double dx, double d
                       Y0 + (double)w1 * (Y1 - Y0) + (double)w2 * (Y1 - Y0));
 }
 
-// Three blocks per SM (80 registers, a few bytes of spill) measure faster
-// than two without spill: the kernel is latency-bound.
-__global__ void __launch_bounds__(kSearchThreads, 3)
+// The kernel is latency-bound: blocks of 128 threads, six per SM (80
+// registers, a few bytes of spill), measure faster than fewer, larger blocks
+// or a spill-free register budget, as more independent barrier groups keep
+// the schedulers busy.
+__global__ void __launch_bounds__(kSearchThreads, 6)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
                Hit* __restrict__ hits, int64_t hit_cap, Work64* __restrict__ work,
