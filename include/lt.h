@@ -256,6 +256,13 @@ typedef struct {
 lt_status lt_profile_enable(lt_model* model, int on);
 lt_status lt_profile_read(lt_model* model, lt_profile* out, int reset);
 
+/* Like lt_profile_enable, for a subset of the stages: bit k of mask brackets
+ * stage k (0 deflection, 1 search, 2 FP64 resolution, 3 barycentres + chi^2);
+ * 0 turns timing off.  Each bracketed stage records two events per chunk on
+ * the stream, so timing only the stage of interest keeps the overhead of a
+ * measured evaluation small.  Errors: LT_ERR_INVALID_ARG. */
+lt_status lt_profile_stages(lt_model* model, uint32_t mask);
+
 /* Allocation-free deflection grid, for callers that cannot allocate device
  * memory (code inside an allocator hook or memory-pool callback, plugins of
  * an application that owns every device allocation, processes that reserve

@@ -101,7 +101,7 @@ struct lt_model {
   uint64_t graph_epoch = 0;
   uint64_t ws_epoch = 1;  // bumped whenever a workspace captured by a graph moves
   // optional per-kernel event timing
-  bool prof_on = false;
+  unsigned prof_mask = 0;  // stages bracketed by events (bit k = stage k)
   struct ProfRec {
     int kind;
     cudaEvent_t e0, e1;
@@ -149,7 +149,7 @@ struct ProfScope {
   ProfScope(lt_model* m_, cudaStream_t st_, int kind_, double np = 0.0, int fp64_ = 0,
             int kernels_ = 1)
       : m(m_), st(st_), kind(kind_), node_pot(np), fp64(fp64_), kernels(kernels_) {
-    if (!m->prof_on) return;
+    if (!(m->prof_mask & (1u << kind))) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     e0 = take();
@@ -870,7 +870,14 @@ lt_status lt_model_sync(lt_model* m, uintptr_t stream, lt_stats* stats) {
 
 lt_status lt_profile_enable(lt_model* m, int on) {
   if (!m) return LT_ERR_INVALID_ARG;
-  m->prof_on = on != 0;
+  m->prof_mask = on ? 0xfu : 0u;
+  return LT_OK;
+}
+
+lt_status lt_profile_stages(lt_model* m, uint32_t mask) {
+  if (!m) return LT_ERR_INVALID_ARG;
+  LT_CHECK_ARG(mask <= 0xfu, "stage mask has bits beyond the four stages");
+  m->prof_mask = mask;
   return LT_OK;
 }
 

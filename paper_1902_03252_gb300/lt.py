@@ -27,7 +27,7 @@ EXPORTED = ("lt_model_create", "lt_model_destroy", "lt_last_error", "lt_status_s
             "lt_chi2_grad", "lt_last_matches", "lt_model_sync", "lt_chi2_graph",
             "lt_autotune", "lt_profile_enable", "lt_profile_read", "lt_dls_ds",
             "lt_chi2_source", "lt_last_magnifications", "lt_model_set_shape",
-            "lt_num_shapes", "lt_version")
+            "lt_num_shapes", "lt_profile_stages", "lt_version")
 
 
 class Grid(C.Structure):
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = False):
     L.lt_autotune.argtypes = [vp, C.POINTER(Grid), up, C.POINTER(i32)]
     L.lt_profile_enable.argtypes = [vp, C.c_int]
     L.lt_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
+    L.lt_profile_stages.argtypes = [vp, C.c_uint32]
     L.lt_dls_ds.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double,
                             C.POINTER(C.c_double)]
     for name in EXPORTED:
@@ -128,7 +129,8 @@ def load(build_if_missing: bool = False):
                                             "lt_model_sync", "lt_autotune",
                                             "lt_profile_enable", "lt_profile_read",
                                             "lt_dls_ds", "lt_chi2_source",
-                                            "lt_last_magnifications", "lt_model_set_shape"):
+                                            "lt_last_magnifications", "lt_model_set_shape",
+                                            "lt_profile_stages"):
             f.restype = st
     _lib = L
     return L
@@ -311,9 +313,14 @@ class Model:
         st = self._lib.lt_model_sync(self.h, _stream(stream), C.byref(s))
         return st, {k: getattr(s, k) for k, _ in Stats._fields_}
 
-    def profile(self, on: bool = True):
-        """Enable / disable per-kernel CUDA-event timing of later calls."""
-        self._check(self._lib.lt_profile_enable(self.h, 1 if on else 0), "lt_profile_enable")
+    def profile(self, on: bool = True, stages=None):
+        """Enable / disable per-stage CUDA-event timing of later calls; stages:
+        optional subset of PROFILE_KINDS (default: all)."""
+        if stages is None:
+            self._check(self._lib.lt_profile_enable(self.h, 1 if on else 0), "lt_profile_enable")
+        else:
+            mask = sum(1 << PROFILE_KINDS.index(k) for k in stages) if on else 0
+            self._check(self._lib.lt_profile_stages(self.h, mask), "lt_profile_stages")
 
     def profile_read(self, reset: bool = True):
         """Per-kernel launches and summed milliseconds since the last reset."""

@@ -194,6 +194,29 @@ def test_find_images_cluster(oracle, seed, prec, tol):
     print(f"prec {prec}: stats {stats}, worst position error {worst:.3g}")
 
 
+@pytest.mark.parametrize("prec,tol", [(lt.FP64, 1e-9), (lt.MIXED, 1e-4)])
+def test_find_images_many_sources(oracle, prec, tol):
+    """600 sources: more than one staged chunk of sources in the search
+    kernel (256 at a time), against the oracle's image set and positions."""
+    p = mixed_cluster(21, n_pot=25, half=20.0)
+    grid = (-30.0, -30.0, 60.0 / 299, 60.0 / 299, 300, 300)
+    rng = np.random.default_rng(21)
+    src = rng.uniform(-10, 10, (600, 2))
+    r = rng.uniform(0.3, 0.9, 600)
+    m = lt.Model(p.shape[1], 1, hit_capacity=1 << 15)
+    m.set_params(p[None])
+    st, stats, imgs, n = run_find(m, [grid], src[None], r[None], prec, cap=1 << 15)
+    assert st == lt.LT_OK, (st, stats)
+    H, U = oracle.find_images(p, grid, src, r, n_threads=8, capacity=1 << 15)
+    assert not U
+    assert to_set(imgs[0]) == oracle_set(H)
+    ref = {(h["src"], h["tri"]): h for h in H}
+    worst = max(max(abs(rec["x"] - ref[(int(rec["src"]), int(rec["tri"]))]["x"]),
+                    abs(rec["y"] - ref[(int(rec["src"]), int(rec["tri"]))]["y"])) for rec in imgs[0])
+    assert worst <= tol, worst
+    m.close()
+
+
 # ------------------------------------------------------------------- chi^2
 def check_chi2(oracle, w, o, prec, grids=None, graph=False):
     grids = grids or [g.as_tuple() for g in w.grids]
