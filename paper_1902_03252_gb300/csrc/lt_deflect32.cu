@@ -10,8 +10,6 @@
 
 namespace lt {
 
-// Safety factor applied to the first-order error bound of every node.
-constexpr float kBoundSafety = 2.0f;
 constexpr int kChunk32 = 256;  // potentials staged in shared memory at a time
 
 // --------------------------------------------------------------- deflection

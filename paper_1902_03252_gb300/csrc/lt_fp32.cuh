@@ -20,19 +20,27 @@ __device__ __forceinline__ void sis32(const float4* f, float P, float x, float y
   err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
 }
 
-// One SIE (Algorithm 1).
+// One SIE (Algorithm 1), with the axis weights folded into the rotation:
+// u = sqrt(1-eps) x', v = sqrt(1+eps) y' (so R^2 = u^2 + v^2), and the
+// rotation back applied to (b0 sqrt(1-eps) u, b0 sqrt(1+eps) v) before the
+// division by R:
+//   alpha_x += (b0 sqrt(1-eps) c u - b0 sqrt(1+eps) s v) / R,
+//   alpha_y += (b0 sqrt(1+eps) c v + b0 sqrt(1-eps) s u) / R,
+// which is Algorithm 1's (1 -+ eps) b0 x'/R rotated by -phi.  Record:
+// f[0] = {cx, cy, sqrt(1-eps) c, sqrt(1-eps) s},
+// f[1] = {sqrt(1+eps) c, sqrt(1+eps) s, b0 sqrt(1-eps) c, b0 sqrt(1+eps) s},
+// f[2] = {b0 sqrt(1+eps) c, b0 sqrt(1-eps) s, 0, 0}.
 __device__ __forceinline__ void sie32(const float4* f, float P, float x, float y, float& ax,
                                       float& ay, float& err) {
-  float dx = x - f[0].x, dy = y - f[0].y;
-  float c = f[0].z, s = f[0].w;
-  float xp = fmaf(dx, c, dy * s);
-  float yp = fmaf(dy, c, -(dx * s));
-  float R2 = fmaf(xp * xp, f[1].x, yp * yp * f[1].y);
-  float ri = R2 > 0.0f ? rsqrtf(R2) : 0.0f;
-  float gx = f[1].z * xp * ri;
-  float gy = f[1].w * yp * ri;
-  ax = fmaf(gx, c, fmaf(-gy, s, ax));
-  ay = fmaf(gy, c, fmaf(gx, s, ay));
+  const float dx = x - f[0].x, dy = y - f[0].y;
+  const float u = fmaf(dx, f[0].z, dy * f[0].w);
+  const float v = fmaf(dy, f[1].x, -(dx * f[1].y));
+  const float R2 = fmaf(u, u, v * v);
+  const float ri = R2 > 0.0f ? rsqrtf(R2) : 0.0f;
+  const float t1 = fmaf(f[1].z, u, -(f[1].w * v));
+  const float t2 = fmaf(f[2].x, v, f[2].y * u);
+  ax = fmaf(ri, t1, ax);
+  ay = fmaf(ri, t2, ay);
   err = fmaf(P, ri, err);
   err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
 }

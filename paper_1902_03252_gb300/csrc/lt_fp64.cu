@@ -134,9 +134,11 @@ __global__ void __launch_bounds__(kPrepThreads)
       Q = 8.0 * p.b0;
     } else if (kind == LT_SIE) {
       const double ge = (1.0 + p.e) / (1.0 - p.e);
-      f.f[0] = make_float4(cx, cy, c, s);
-      f.f[1] = make_float4((float)(1.0 - p.e), (float)(1.0 + p.e), (float)(p.b0 * (1.0 - p.e)),
-                           (float)(p.b0 * (1.0 + p.e)));
+      const double r1 = sqrt(1.0 - p.e), r2 = sqrt(1.0 + p.e);
+      f.f[0] = make_float4(cx, cy, (float)(r1 * p.c), (float)(r1 * p.s));
+      f.f[1] = make_float4((float)(r2 * p.c), (float)(r2 * p.s), (float)(p.b0 * r1 * p.c),
+                           (float)(p.b0 * r2 * p.s));
+      f.f[2] = make_float4((float)(p.b0 * r2 * p.c), (float)(p.b0 * r1 * p.s), 0.f, 0.f);
       f.f[4] = make_float4((float)(4.0 * p.b0 * ge), 0.f, 0.f, 0.f);
       Q = 16.0 * p.b0 * ge;
     } else {

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kNT)
       const int64_t n = base + m * kNT + threadIdx.x;
       if (n < nodes) {
         alpha[n] = make_float2(AX[m], AY[m]);
-        if (err) err[n] = 2.0f * kU32 * (ER[m] + sg.q_tot);
+        if (err) err[n] = kBoundSafety * kU32 * (ER[m] + sg.q_tot);
       }
     }
   }
