@@ -79,6 +79,7 @@ struct lt_model {
   int64_t* d_match_tri = nullptr;
   int32_t* d_match_hit = nullptr;
   double* d_match_xy = nullptr;
+  double* d_chi2_terms = nullptr;  // chi^2 term of each observed image [batch][n_obs]
   // FP64 resolution scratch (node table, vertex slots, distinct-node list)
   ResolveScratch rs{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
   size_t rs_vslot_alloc = 0;
@@ -317,14 +318,17 @@ lt_status ensure_obs(lt_model* m, int n_obs, int n_sys) {
     if (m->d_match_xy) LT_CUDA(cudaFree(m->d_match_xy));
     if (m->d_adj_lam) LT_CUDA(cudaFree(m->d_adj_lam));
     if (m->d_adj_pts) LT_CUDA(cudaFree(m->d_adj_pts));
+    if (m->d_chi2_terms) LT_CUDA(cudaFree(m->d_chi2_terms));
     m->d_beta_obs = nullptr; m->d_match_tri = nullptr; m->d_match_hit = nullptr;
     m->d_match_xy = nullptr; m->d_adj_lam = nullptr; m->d_adj_pts = nullptr;
+    m->d_chi2_terms = nullptr;
     LT_CUDA(cudaMalloc(&m->d_beta_obs, sizeof(double) * 2 * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_match_tri, sizeof(int64_t) * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_match_hit, sizeof(int32_t) * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_match_xy, sizeof(double) * 2 * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_adj_lam, sizeof(double2) * (size_t)m->batch * n_obs));
     LT_CUDA(cudaMalloc(&m->d_adj_pts, sizeof(AdjPt) * 4 * (size_t)m->batch * n_obs));
+    LT_CUDA(cudaMalloc(&m->d_chi2_terms, sizeof(double) * (size_t)m->batch * n_obs));
     m->obs_alloc = n_obs;
   }
   if (n_sys > m->sys_alloc) {
@@ -471,10 +475,10 @@ lt_status enqueue_chi2(lt_model* m, const lt_obs& obs, int precision, double* ch
     const Chunk& c = m->plan.chunks[ci];
     s = enqueue_search(m, ci, precision, src, hc, st, ci == 0 ? m->ev_join : nullptr);
     if (s != LT_OK) return s;
-    ProfScope ps(m, st, 3);
+    ProfScope ps(m, st, 3, 0.0, 0, 2);  // k_chi2_match, k_chi2_sum
     LT_CUDA(launch_chi2(m->d_hits + (size_t)c.b0 * hc, m->d_hit_count + c.b0, c.b1 - c.b0, hc,
-                        c.b0, m->d_plan_grids + c.b0, obs, chi2_out, m->d_match_tri,
-                        m->d_match_hit, m->d_match_xy, st));
+                        c.b0, m->d_plan_grids + c.b0, obs, chi2_out, m->d_chi2_terms,
+                        m->d_match_tri, m->d_match_hit, m->d_match_xy, st));
   }
   m->last_nobs = obs.n_obs;
   m->last_nsys = obs.n_sys;
@@ -568,7 +572,8 @@ void lt_model_destroy(lt_model* m) {
                   m->d_nodes, m->d_hits, m->d_work, m->d_hit_count, m->d_work_count,
                   m->d_plan_grids, m->d_plan_items, m->d_beta_obs, m->d_bary, m->d_match_tri,
                   m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched,
-                  m->d_src_beta, m->d_src_mu, m->d_src_bary, m->rs.keys, m->rs.hval,
+                  m->d_src_beta, m->d_src_mu, m->d_src_bary, m->d_chi2_terms, m->rs.keys,
+                  m->rs.hval,
                   m->rs.vslot, m->rs.ulist, m->rs.n_unique};
   for (void* p : ptrs)
     if (p) cudaFree(p);

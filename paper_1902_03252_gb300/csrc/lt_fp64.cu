@@ -11,7 +11,7 @@
 //                 certify and of FP32 hits whose position bound is too large.
 //   k_bary_obs / k_bary_sys   barycentres of the observed systems.
 //   k_sort_hits   images of each sample in (source, triangle) order.
-//   k_chi2        nearest-image matching and the chi^2 of Eq. 11.
+//   k_chi2_match / k_chi2_sum   nearest-image matching and the chi^2 of Eq. 11.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -666,84 +666,95 @@ cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_coun
 }
 
 // -------------------------------------------------------------------- chi^2
-// One block per sample.  Each thread takes observed images m = tid, tid+NT,
-// ..., finds the nearest predicted image of the same system (ties to the
-// lower triangle id) and adds |x_obs - x|^2/sigma^2 (or the penalty
-// (L_diag/sigma)^2 when the system has no image); the per-thread sums are
-// reduced by warp shuffles in a fixed order, then across warps.
+// Each observed image is matched to the nearest predicted image of its
+// system (ties to the lower triangle id) and adds |x_obs - x|^2/sigma^2, or
+// the penalty (L_diag/sigma)^2 when the system has no image.
 constexpr int kChi2Threads = 128;
 
-// The hit list is staged through shared memory in chunks (each thread's scan
-// over the hits would otherwise be a chain of dependent global-memory
-// latencies); each thread keeps its observed image's best match so far.
-constexpr int kChi2Stage = 512;
+// Matching: one warp per (sample, observed image).  The lanes scan the hits
+// of the sample (lane l takes hits l, l + 32, ...), each keeping the nearest
+// predicted image of the observed image's system, ties to the lower triangle
+// id; the warp then reduces the lanes' candidates by the same rule, which
+// orders (distance^2, triangle) totally, so the result does not depend on the
+// reduction order.  The term of Eq. 11 (or the no-image penalty) goes to
+// terms[]; k_chi2_sum adds a sample's terms in a fixed order.
+constexpr int kMatchThreads = 128;
 
-struct HitXY {
-  double x, y;
-  int64_t tri;
-  int32_t src, pad;
-};
+__device__ __forceinline__ bool better(double d2, int64_t tri, double bd, int64_t btri) {
+  return bd < 0.0 || d2 < bd || (d2 == bd && tri < btri);
+}
 
-__global__ void __launch_bounds__(kChi2Threads)
-    k_chi2(const Hit* __restrict__ hits, const unsigned long long* __restrict__ hit_count,
-           int64_t hit_cap, int sample_base, const SampleGrid* __restrict__ grids, lt_obs obs,
-           double* __restrict__ chi2, int64_t* __restrict__ match_tri,
-           int32_t* __restrict__ match_hit, double* __restrict__ match_xy) {
-  __shared__ double wsum[kChi2Threads / 32];
-  __shared__ HitXY sh[kChi2Stage];
-  const int b = blockIdx.x;
+__global__ void __launch_bounds__(kMatchThreads)
+    k_chi2_match(const Hit* __restrict__ hits, const unsigned long long* __restrict__ hit_count,
+                 int64_t hit_cap, int n_samples, int sample_base,
+                 const SampleGrid* __restrict__ grids, lt_obs obs, double* __restrict__ terms,
+                 int64_t* __restrict__ match_tri, int32_t* __restrict__ match_hit,
+                 double* __restrict__ match_xy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * kMatchThreads + threadIdx.x) >> 5;
+  if (wid >= (int64_t)n_samples * obs.n_obs) return;  // warp-uniform
+  const int b = (int)(wid / obs.n_obs);
+  const int m = (int)(wid - (int64_t)b * obs.n_obs);
   const int sample = sample_base + b;
-  const SampleGrid g = grids[b];
   const int64_t n = (int64_t)min((unsigned long long)hit_cap, hit_count[b]);
   const Hit* hb = hits + (int64_t)b * hit_cap;
-  const double Lx = (g.nx - 1) * g.dx, Ly = (g.ny - 1) * g.dy;
-  const double diag = sqrt(Lx * Lx + Ly * Ly);
-  double acc = 0.0;
-  for (int m0 = 0; m0 < obs.n_obs; m0 += kChi2Threads) {
-    const int m = m0 + threadIdx.x;
-    const bool act = m < obs.n_obs;
-    const int i = act ? obs.sys[m] : -1;
-    const double ox = act ? obs.x[m] : 0.0, oy = act ? obs.y[m] : 0.0;
-    int64_t best = -1, best_tri = 0;
-    double bd = 0.0;
-    for (int64_t h0 = 0; h0 < n; h0 += kChi2Stage) {
-      const int cn = (int)min((int64_t)kChi2Stage, n - h0);
-      __syncthreads();
-      for (int v = threadIdx.x; v < cn; v += kChi2Threads) {
-        const Hit& H = hb[h0 + v];
-        sh[v] = HitXY{H.x, H.y, H.tri, H.src, 0};
-      }
-      __syncthreads();
-      for (int v = 0; v < cn; ++v) {
-        if (sh[v].src != i) continue;
-        const double ex = ox - sh[v].x, ey = oy - sh[v].y;
-        const double d2 = ex * ex + ey * ey;
-        if (best < 0 || d2 < bd || (d2 == bd && sh[v].tri < best_tri)) {
-          best = h0 + v;
-          best_tri = sh[v].tri;
-          bd = d2;
-        }
-      }
-    }
-    if (act) {
-      const double sg = obs.sigma[m];
-      double term;
-      const int64_t o = (int64_t)sample * obs.n_obs + m;
-      if (best < 0) {
-        const double t = diag / sg;
-        term = t * t;
-        if (match_tri) match_tri[o] = -1;
-        if (match_hit) match_hit[o] = -1;
-        if (match_xy) { match_xy[2 * o] = 0.0; match_xy[2 * o + 1] = 0.0; }
-      } else {
-        term = bd / (sg * sg);
-        if (match_tri) match_tri[o] = hb[best].tri;
-        if (match_hit) match_hit[o] = (int32_t)best;
-        if (match_xy) { match_xy[2 * o] = hb[best].x; match_xy[2 * o + 1] = hb[best].y; }
-      }
-      acc = acc + term;
+  const int i = obs.sys[m];
+  const double ox = obs.x[m], oy = obs.y[m];
+  double bd = -1.0;  // -1: none yet
+  int64_t btri = 0, bh = -1;
+  for (int64_t h = lane; h < n; h += 32) {
+    if (hb[h].src != i) continue;
+    const double ex = ox - hb[h].x, ey = oy - hb[h].y;
+    const double d2 = ex * ex + ey * ey;
+    const int64_t tri = hb[h].tri;
+    if (better(d2, tri, bd, btri)) {
+      bd = d2;
+      btri = tri;
+      bh = h;
     }
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double od = __shfl_xor_sync(0xffffffffu, bd, off);
+    const long long ot = __shfl_xor_sync(0xffffffffu, (long long)btri, off);
+    const long long oh = __shfl_xor_sync(0xffffffffu, (long long)bh, off);
+    if (od >= 0.0 && better(od, ot, bd, btri)) {
+      bd = od;
+      btri = ot;
+      bh = oh;
+    }
+  }
+  if (lane == 0) {
+    const double sg = obs.sigma[m];
+    const int64_t o = (int64_t)sample * obs.n_obs + m;
+    double term;
+    if (bh < 0) {
+      const SampleGrid g = grids[b];
+      const double Lx = (g.nx - 1) * g.dx, Ly = (g.ny - 1) * g.dy;
+      const double t = sqrt(Lx * Lx + Ly * Ly) / sg;
+      term = t * t;
+      if (match_tri) match_tri[o] = -1;
+      if (match_hit) match_hit[o] = -1;
+      if (match_xy) { match_xy[2 * o] = 0.0; match_xy[2 * o + 1] = 0.0; }
+    } else {
+      term = bd / (sg * sg);
+      if (match_tri) match_tri[o] = hb[bh].tri;
+      if (match_hit) match_hit[o] = (int32_t)bh;
+      if (match_xy) { match_xy[2 * o] = hb[bh].x; match_xy[2 * o + 1] = hb[bh].y; }
+    }
+    terms[o] = term;
+  }
+}
+
+// chi^2 of each sample: thread t adds terms t, t + 128, ..., then warp
+// shuffles and the warps in order (a fixed order).
+__global__ void __launch_bounds__(kChi2Threads)
+    k_chi2_sum(int sample_base, int n_obs, const double* __restrict__ terms,
+               double* __restrict__ chi2) {
+  __shared__ double wsum[kChi2Threads / 32];
+  const int sample = sample_base + blockIdx.x;
+  const double* tb = terms + (int64_t)sample * n_obs;
+  double acc = 0.0;
+  for (int m = threadIdx.x; m < n_obs; m += kChi2Threads) acc = acc + tb[m];
   for (int off = 16; off > 0; off >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -756,11 +767,17 @@ __global__ void __launch_bounds__(kChi2Threads)
 
 cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, int n_samples,
                         int64_t hit_cap, int sample_base, const SampleGrid* grids,
-                        const lt_obs& obs, double* chi2, int64_t* match_tri, int32_t* match_hit,
-                        double* match_xy, cudaStream_t st) {
+                        const lt_obs& obs, double* chi2, double* terms, int64_t* match_tri,
+                        int32_t* match_hit, double* match_xy, cudaStream_t st) {
   if (n_samples <= 0) return cudaSuccess;
-  k_chi2<<<n_samples, kChi2Threads, 0, st>>>(hits, hit_count, hit_cap, sample_base, grids, obs,
-                                             chi2, match_tri, match_hit, match_xy);
+  const int64_t warps = (int64_t)n_samples * obs.n_obs;
+  const int64_t blocks = (warps * 32 + kMatchThreads - 1) / kMatchThreads;
+  k_chi2_match<<<(unsigned)blocks, kMatchThreads, 0, st>>>(hits, hit_count, hit_cap, n_samples,
+                                                            sample_base, grids, obs, terms,
+                                                            match_tri, match_hit, match_xy);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_chi2_sum<<<n_samples, kChi2Threads, 0, st>>>(sample_base, obs.n_obs, terms, chi2);
   return cudaGetLastError();
 }
 

@@ -363,7 +363,7 @@ cudaError_t launch_paper_fp64(const Pot64* pot64, int n_pot, const lt_grid& g, c
                               cudaStream_t st);
 cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, int n_samples,
                         int64_t hit_cap, int sample_base, const SampleGrid* grids,
-                        const lt_obs& obs, double* chi2, int64_t* match_tri, int32_t* match_hit,
-                        double* match_xy, cudaStream_t st);
+                        const lt_obs& obs, double* chi2, double* terms, int64_t* match_tri,
+                        int32_t* match_hit, double* match_xy, cudaStream_t st);
 
 }  // namespace lt

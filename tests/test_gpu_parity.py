@@ -262,6 +262,31 @@ def test_chi2_batched_uneven(oracle):
     check_chi2(oracle, w, o, lt.MIXED, grids=grids)
 
 
+def test_chunked_batch_matches_one_chunk(monkeypatch):
+    """A node-workspace budget of 2 MB puts every sample of the batch in a
+    chunk of its own (separate launches, item tables, FP64 node tables):
+    the results equal those of one chunk for the whole batch, bit for bit."""
+    w = W.c3(batch=8)
+    o = load_obs("c3")
+    rng = np.random.default_rng(5)
+    grids = [W.Grid.square(200.0, int(n)).as_tuple() for n in rng.integers(300, 700, 8)]
+    obs = lt.Observations.from_dict(o)
+    res = []
+    for budget in (None, "2"):
+        if budget:
+            monkeypatch.setenv("LT_WORKSPACE_MB", budget)
+        m = lt.Model(w.n_pot, w.batch)
+        m.set_params(w.params)
+        c2, g = m.chi2_grad(grids, obs)
+        st, stats = m.sync()
+        assert st == lt.LT_OK
+        mt, mxy, _ = m.last_matches(len(o["x"]), len(o["dls_ds"]))
+        res.append((c2.cpu().numpy(), g.cpu().numpy(), mt.cpu().numpy(), mxy.cpu().numpy()))
+        m.close()
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_graph_replay_matches_direct(oracle):
     w = W.c4()
     o = load_obs("c4")
