@@ -234,9 +234,11 @@ lt_status lt_model_set_shape(lt_model* model, int32_t shape);
 int32_t lt_num_shapes(void);
 
 /* Autotune the FP32 deflection kernel's launch shape for this model's
- * potential mix on a representative grid (times each candidate with CUDA
- * events on `stream`) and keep the fastest for later calls.  *choice
- * (optional) receives the index of the chosen variant. */
+ * potential mix (sample 0) on a representative grid: each candidate shape's
+ * kernel alone is timed with CUDA events on `stream`, the minimum of five
+ * launches after a warm-up; a later candidate replaces an earlier one only
+ * when it is faster by more than 0.5 %.  The fastest is kept for later calls;
+ * *choice (optional) receives its index.  Synchronises the stream. */
 lt_status lt_autotune(lt_model* model, const lt_grid* grid, uintptr_t stream, int32_t* choice);
 
 /* Per-kernel timing of later compute calls (off by default).  When enabled,
