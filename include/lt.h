@@ -168,8 +168,10 @@ lt_status lt_model_set_params(lt_model* model, const double* params, int on_devi
  * the lensing potential summed over all potentials at every node).
  * alpha_out: device, [ny][nx][2] of float (LT_PREC_MIXED) or double
  * (LT_PREC_FP64, LT_PREC_PAPER).  err_out: optional device [ny][nx] float
- * receiving the FP32 running error bound of each node (LT_PREC_MIXED) or the
- * FP64-recomputation map (LT_PREC_PAPER); NULL with LT_PREC_FP64.
+ * receiving the FP32 running error bound of each node (LT_PREC_MIXED; 1e30
+ * at a node whose FP32 coordinates coincide with an SIS or SIE centre, where
+ * the deflection's direction is undefined) or the FP64-recomputation map
+ * (LT_PREC_PAPER); NULL with LT_PREC_FP64.
  * Errors: LT_ERR_INVALID_ARG. */
 lt_status lt_deflect_grid(lt_model* model, int32_t sample, const lt_grid* grid,
                           lt_precision precision, void* alpha_out, float* err_out,

@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
         float4 val = pb[c0 + k].f[w];
         if (w == 4) {  // translation-error coefficient for this grid
           float4 h = pb[c0 + k].f[0];
-          val.x = val.x * (theta1 + fabsf(h.x) + fabsf(h.y));
+          // strictly positive, so that P times an infinite 1/R (a node on an
+          // SIS/SIE centre) is +inf, never NaN, even for a zero-mass potential
+          val.x = fmaf(val.x, theta1 + fabsf(h.x) + fabsf(h.y), 1e-30f);
         }
         sp[v] = val;
       }
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
       int64_t n = base + m * NT + threadIdx.x;
       if (n < nodes)
         node_out[g.node_off + n] =
-            make_float4(AX[m], AY[m], kBoundSafety * kU32 * (ER[m] + qs), 0.0f);
+            make_float4(AX[m], AY[m], node_bound(ER[m] + qs), 0.0f);
     }
   }
 }

@@ -12,11 +12,14 @@ __device__ __forceinline__ void sis32(const float4* f, float P, float x, float y
                                       float& ay, float& err) {
   float dx = x - f[0].x, dy = y - f[0].y;
   float R2 = fmaf(dx, dx, dy * dy);
-  float ri = R2 > 0.0f ? rsqrtf(R2) : 0.0f;
+  // rr is +inf on the centre: there the direction of alpha is undefined and
+  // the bound term P rr makes the node's bound infinite (never certified)
+  const float rr = rsqrtf(R2);
+  const float ri = R2 > 0.0f ? rr : 0.0f;
   float g = f[0].z * ri;
   ax = fmaf(g, dx, ax);
   ay = fmaf(g, dy, ay);
-  err = fmaf(P, ri, err);
+  err = fmaf(P, rr, err);
   err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
 }
 
@@ -36,12 +39,13 @@ __device__ __forceinline__ void sie32(const float4* f, float P, float x, float y
   const float u = fmaf(dx, f[0].z, dy * f[0].w);
   const float v = fmaf(dy, f[1].x, -(dx * f[1].y));
   const float R2 = fmaf(u, u, v * v);
-  const float ri = R2 > 0.0f ? rsqrtf(R2) : 0.0f;
+  const float rr = rsqrtf(R2);  // +inf on the centre: an infinite bound there
+  const float ri = R2 > 0.0f ? rr : 0.0f;
   const float t1 = fmaf(f[1].z, u, -(f[1].w * v));
   const float t2 = fmaf(f[2].x, v, f[2].y * u);
   ax = fmaf(ri, t1, ax);
   ay = fmaf(ri, t2, ay);
-  err = fmaf(P, ri, err);
+  err = fmaf(P, rr, err);
   err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
 }
 

@@ -59,6 +59,13 @@ static_assert(sizeof(Pot32) == 80, "Pot32 layout");
 // actual error to bound over all test grids is below 0.05.)
 constexpr float kBoundSafety = 1.25f;
 
+// A node's bound from its accumulated terms (in units of the unit roundoff),
+// capped at 1e30: a node on an SIS/SIE centre has an infinite term, and a
+// finite cap keeps every later product (r E with r = 0 included) a number.
+__device__ __forceinline__ float node_bound(float terms) {
+  return fminf(kBoundSafety * kU32 * terms, 1e30f);
+}
+
 // Per-sample kind segments of the FP32 records: [n_sis, n_piemd, n_sie, 0]
 // and the static part of the error bound, sum_k errQ_k (float).
 struct Seg32 {

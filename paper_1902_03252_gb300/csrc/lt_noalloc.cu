@@ -95,7 +95,9 @@ __global__ void __launch_bounds__(kNT)
         float4 val = pot32[c0 + k].f[w];
         if (w == 4) {
           const float4 h = pot32[c0 + k].f[0];
-          val.x = val.x * (theta1 + fabsf(h.x) + fabsf(h.y));
+          // strictly positive, so that P times an infinite 1/R (a node on an
+          // SIS/SIE centre) is +inf, never NaN, even for a zero-mass potential
+          val.x = fmaf(val.x, theta1 + fabsf(h.x) + fabsf(h.y), 1e-30f);
         }
         sp[v] = val;
       }
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(kNT)
       const int64_t n = base + m * kNT + threadIdx.x;
       if (n < nodes) {
         alpha[n] = make_float2(AX[m], AY[m]);
-        if (err) err[n] = kBoundSafety * kU32 * (ER[m] + sg.q_tot);
+        if (err) err[n] = node_bound(ER[m] + sg.q_tot);
       }
     }
   }

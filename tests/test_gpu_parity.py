@@ -92,6 +92,55 @@ def test_deflect_mixed_within_running_bound(oracle, seed):
     assert ratio.max() <= 1.0
 
 
+def test_deflect_bound_adversarial(oracle):
+    """The running FP32 bound on the hardest inputs: PIEMD with ellipticity
+    up to 0.9 (atanh's sensitivity grows as 1/q^2), cores from 1e-3" to 3",
+    cuts from 1.5 to 1e4 times the core, SIE with eps up to 0.9, SIS; nodes
+    on the potentials' centres, on their symmetry axes and within a core
+    radius of them, far from the grid origin (|theta| up to 200")."""
+    rng = np.random.default_rng(77)
+    n = 60
+    p = np.zeros((8, n))
+    p[0] = rng.choice([W.SIS, W.PIEMD, W.SIE], n, p=[0.2, 0.6, 0.2])
+    p[1:3] = rng.uniform(-150, 150, (2, n))
+    p[3] = np.where(p[0] == W.SIS, 0.0, rng.uniform(0.0, 0.9, n))
+    p[4] = rng.uniform(0, np.pi, n)
+    p[5] = 10 ** rng.uniform(-3, 0.5, n)
+    p[6] = p[5] * 10 ** rng.uniform(np.log10(1.5), 4, n)
+    p[7] = 10 ** rng.uniform(1.5, 3.1, n)
+    # nodes: each potential's centre, points on its rotated axes at 0.3, 1, 3
+    # core radii and 1, 10 arcsec, snapped to a fine grid around it
+    xs, ys = [], []
+    for k in range(n):
+        c, s = np.cos(p[4, k]), np.sin(p[4, k])
+        for rad in (0.0, 0.3 * p[5, k], p[5, k], 3 * p[5, k], 1.0, 10.0):
+            for ax in ((c, s), (-s, c)):
+                xs.append(p[1, k] + rad * ax[0])
+                ys.append(p[2, k] + rad * ax[1])
+    xs, ys = np.asarray(xs), np.asarray(ys)
+    # one grid per potential neighbourhood would be many calls: evaluate the
+    # points as a 1-row grid each (a grid's node coordinates are x0 + i dx)
+    m = lt.Model(n, 1)
+    m.set_params(p[None])
+    worst = 0.0
+    for x, y in zip(xs, ys):
+        grid = (float(x) - 1e-3, float(y), 1e-3, 1.0, 3, 1)
+        a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+        a = a.cpu().numpy().astype(np.float64).reshape(-1, 2)
+        e = e.cpu().numpy().astype(np.float64).reshape(-1)
+        gx = grid[0] + np.arange(3) * grid[2]
+        ax, ay, _ = oracle.alpha_points(p, gx, np.full(3, grid[1]))
+        d = np.maximum(np.abs(a[:, 0] - ax), np.abs(a[:, 1] - ay))
+        # 1e30 only where a node's FP32 coordinates fall on an SIS/SIE centre
+        assert np.all(np.isfinite(e)) and np.all(d <= e), (x, y, d, e)
+        fin = e < 1e29
+        if fin.any():
+            worst = max(worst, float((d[fin] / e[fin]).max()))
+    assert m.sync()[0] == lt.LT_OK
+    print(f"adversarial nodes: largest error / bound {worst:.3g}")
+    m.close()
+
+
 @pytest.mark.parametrize("shape", range(5))
 def test_deflect_every_shape_within_bound(oracle, shape):
     """Every launch shape of the FP32 deflection on 300 potentials of all
