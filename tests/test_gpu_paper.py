@@ -136,3 +136,54 @@ def test_paper_mixed_rule(oracle):
     rx, ry, _ = oracle.alpha_points(p, x, y)
     d = np.maximum(np.abs(ap[uj[sel], ui[sel], 0] - rx), np.abs(ap[uj[sel], ui[sel], 1] - ry))
     assert d.max() <= g["total_sp_bound"], d.max()
+
+
+def test_hff_full_size_sampled(oracle):
+    """The paper's benchmark grid at full size (6730^2 pixels at 0.03", 702
+    SIE, Sect. 4) in all three precisions, on sampled pixels against the
+    oracle: FP32 within each pixel's running bound and within the paper's
+    total single-precision bound outside its DP patches, FP64 within 1e-12 of
+    sum |alpha_k|, the paper's rule exact in FP64 where it flags a pixel and
+    equal to the FP32 grid elsewhere."""
+    from paper_1902_03252_gb300 import workloads as W
+    g = json.load(open(GOLDEN))
+    w = W.hff()
+    grid = w.grids[0].as_tuple()
+    nx, ny = grid[4], grid[5]
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    a32, e32 = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+    rng = np.random.default_rng(99)
+    idx = rng.integers(0, nx * ny, 4000)
+    jj, ii = np.divmod(idx, nx)
+    x = grid[0] + ii * grid[2]
+    y = grid[1] + jj * grid[3]
+    rx, ry, asum = oracle.alpha_points(w.params[0], x, y)
+    A32 = a32.reshape(-1, 2)[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.float64)
+    E32 = e32.reshape(-1)[torch.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.float64)
+    d32 = np.maximum(np.abs(A32[:, 0] - rx), np.abs(A32[:, 1] - ry))
+    assert np.all(d32 <= E32), (d32 / E32).max()
+    # outside the paper's DP patches (200 pixels around cluster halos, 10
+    # around galaxies) the FP32 error stays within its total SP bound
+    outside = np.ones(idx.size, bool)
+    for k in range(w.n_pot):
+        half = 200 if k < 2 else 10
+        ci = np.rint((w.params[0, 1, k] - grid[0]) / grid[2])
+        cj = np.rint((w.params[0, 2, k] - grid[1]) / grid[3])
+        outside &= ~((np.abs(ii - ci) <= half) & (np.abs(jj - cj) <= half))
+    assert d32[outside].max() <= g["total_sp_bound"], d32[outside].max()
+    del a32, e32
+    a64 = m.deflect_grid(grid, precision=lt.FP64)
+    A64 = a64.reshape(-1, 2)[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    d64 = np.maximum(np.abs(A64[:, 0] - rx), np.abs(A64[:, 1] - ry))
+    assert np.all(d64 <= 1e-12 * (asum + 1.0)), d64.max()
+    del a64
+    ap, flag = m.deflect_grid(grid, precision=lt.PAPER, with_error=True)
+    AP = ap.reshape(-1, 2)[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    F = flag.reshape(-1)[torch.as_tensor(idx, device="cuda")].cpu().numpy() > 0
+    dP = np.maximum(np.abs(AP[:, 0] - rx), np.abs(AP[:, 1] - ry))
+    assert np.all(dP[F] <= 1e-12 * (asum[F] + 1.0))
+    assert np.array_equal(AP[~F], A32[~F])
+    st, stats = m.sync()
+    assert st == lt.LT_OK
+    m.close()
