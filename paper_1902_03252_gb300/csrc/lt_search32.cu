@@ -91,13 +91,17 @@ __device__ __forceinline__ void warp_append_work(bool flag, const Work64& wk, Wo
   }
 }
 
+// Warp-wide float minimum / maximum in one instruction (sm_100 and later);
+// exact, like the butterfly of shuffles it replaces.
 __device__ __forceinline__ float warp_min(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  float r;
+  asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
 }
 __device__ __forceinline__ float warp_max(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  float r;
+  asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
 }
 
 struct StripBox {
@@ -105,14 +109,6 @@ struct StripBox {
   int any, pad;
 };
 
-// One work item = 256 consecutive cells, 8 warps of 32 ("strips").  For each
-// chunk of sources: (1) every (strip, source) pair is tested once, by one
-// thread, against a conservative source-plane box of the strip,
-//   beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x]
-// (the same in y) widened by the strip's largest vertex uncertainty; the
-// surviving sources of each strip are compacted into a shared list; (2) each
-// warp runs the per-cell test only for its strip's survivors.  Most pairs
-// never reach the per-cell arithmetic.
 // Image position of an FP32-certified hit, interpolated in FP64 from the
 // triangle's node coordinates: T0 = (X0,Y0), (X1,Y0), (X1,Y1); T1 = (X0,Y0),
 // (X1,Y1), (X0,Y1); w1, w2 the barycentric weights of the 2nd and 3rd
@@ -130,6 +126,15 @@ __device__ __noinline__ double2 hit_xy(double x0, double y0, double dx, double d
                       Y0 + (double)w1 * (Y1 - Y0) + (double)w2 * (Y1 - Y0));
 }
 
+// One work item = 128 consecutive cells, 4 warps of 32 ("strips").  For each
+// chunk of sources: (1) every (strip, source) pair is tested once, by one
+// thread, against a conservative source-plane box of the strip,
+//   beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x]
+// (the same in y) widened by the strip's largest vertex uncertainty; the
+// surviving sources of each strip are compacted into a shared list; (2) each
+// warp runs the per-cell test only for its strip's survivors.  Most pairs
+// never reach the per-cell arithmetic.
+//
 // The kernel is latency-bound: blocks of 128 threads, six per SM (80
 // registers, a few bytes of spill), measure faster than fewer, larger blocks
 // or a spill-free register budget, as more independent barrier groups keep
