@@ -70,7 +70,7 @@ template <int NPT>
 __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, const float* X,
                                               const float* Y, float* AX, float* AY, float* ER) {
   const float cx = f[0].x, cy = f[0].y, c = f[0].z, s = f[0].w;
-  const float k2 = f[1].w, B = f[3].w;
+  const float k2 = f[1].w, Bc = f[3].w, Bs = f[4].w;
   float tx[NPT], ty[NPT], ux[NPT], uy[NPT], ra[NPT], px_[NPT], py_[NPT];
   bool any = false;
 #pragma unroll
@@ -91,10 +91,11 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, const fl
     const float py = (pa + f[2].z) * (ps + f[2].w);
     const float denx = fmaf(k2, x2, px);
     const float deny = fmaf(-k2, y2, py);
+    // the ds coefficients carry sig = sqrt(k2): these are sig tx, sig ty
     tx[m] = __fdividef(xp * dsx, denx);
     ty[m] = __fdividef(yp * dsy, deny);
-    ux[m] = k2 * tx[m] * tx[m];
-    uy[m] = k2 * ty[m] * ty[m];
+    ux[m] = tx[m] * tx[m];
+    uy[m] = ty[m] * ty[m];
     any |= (ux[m] > 1.0f) | (uy[m] > 0.25f);
   }
 #pragma unroll
@@ -127,10 +128,11 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, const fl
   }
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
-    const float gx = B * tx[m] * px_[m];
-    const float gy = B * ty[m] * py_[m];
-    AX[m] = fmaf(gx, c, fmaf(-gy, s, AX[m]));
-    AY[m] = fmaf(gy, c, fmaf(gx, s, AY[m]));
+    // the rotated-frame components are (B/sig) gx, (B/sig) gy
+    const float gx = tx[m] * px_[m];
+    const float gy = ty[m] * py_[m];
+    AX[m] = fmaf(gx, Bc, fmaf(-gy, Bs, AX[m]));
+    AY[m] = fmaf(gy, Bc, fmaf(gx, Bs, AY[m]));
     ER[m] = fmaf(P, ra[m], ER[m]);
     ER[m] = fmaf(f[4].y, fabsf(gx), fmaf(f[4].z, fabsf(gy), ER[m]));
     ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);

@@ -144,17 +144,23 @@ __global__ void __launch_bounds__(kPrepThreads)
     } else {
       const double a = p.a, sc = p.sc, q2 = p.q2, q = p.q;
       const double B = p.scale;
+      // sig = sqrt(k2) is folded into the ds coefficients, so the kernel forms
+      // sig*t directly and (sig t)^2 = k2 t^2 in one product; B/sig and the
+      // rotation back are folded into (Bc, Bs).  For a circular PIEMD (k2 = 0)
+      // sig is 1e-8: then (sig t)^2 < 1e-16 (|t| < 1 there) instead of 0, a
+      // relative change of atan(sig t)/(sig t) far below the FP32 roundoff.
+      const double sig = sqrt(fmax(p.k2, 1e-16)), Bs = B / sig;
       f.f[0] = make_float4(cx, cy, c, s);
       f.f[1] = make_float4((float)q2, (float)(q2 * a * a), (float)(q2 * sc * sc), (float)p.k2);
       f.f[2] = make_float4((float)a, (float)sc, (float)(q2 * a), (float)(q2 * sc));
-      f.f[3] = make_float4((float)(sc - a), (float)(q2 * (sc + a) * (sc - a)),
-                           (float)(q2 * (sc - a)), (float)B);
+      f.f[3] = make_float4((float)(sig * (sc - a)), (float)(sig * q2 * (sc + a) * (sc - a)),
+                           (float)(sig * q2 * (sc - a)), (float)(Bs * p.c));
       const double iq2 = 1.0 / q2;
       const double gy = (14.0 + 17.0 * iq2) * (1.0 + iq2) + 10.0;
-      f.f[4] = make_float4((float)(4.0 * B / q), 80.0f, (float)gy, 0.f);
+      f.f[4] = make_float4((float)(4.0 * B / q), (float)(80.0 * Bs), (float)(gy * Bs),
+                           (float)(Bs * p.s));
       Q = 16.0 * B * iq2;
     }
-    f.f[4].w = (float)Q;
     qsum += (float)Q;
     pot32[(int64_t)b * n_pot + rank] = f;
   }

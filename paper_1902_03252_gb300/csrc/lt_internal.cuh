@@ -41,9 +41,12 @@ static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 //   SIE   : f[0] = {cx, cy, r1 c, r1 s}; f[1] = {r2 c, r2 s, b0 r1 c, b0 r2 s};
 //           f[2] = {b0 r2 c, b0 r1 s, 0, 0} with r1,2 = sqrt(1 -+ eps)
 //   PIEMD : f[0] = {cx, cy, c, s}; f[1] = {q2, q2*a*a, q2*s*s, k2};
-//           f[2] = {a, s, q2*a, q2*s}; f[3] = {s-a, q2(s+a)(s-a), q2(s-a), B}
-//   all   : f[4] = {errP0, errGx, errGy, errQ} (error-bound coefficients; SIS
-//           and SIE use errP0 only, errQ is summed into Seg32::q_tot)
+//           f[2] = {a, s, q2*a, q2*s};
+//           f[3] = {sig(s-a), sig q2(s+a)(s-a), sig q2(s-a), (B/sig) c};
+//           f[4] = {errP0, errGx B/sig, errGy B/sig, (B/sig) s}, sig = sqrt(k2)
+//   SIS/SIE: f[4] = {errP0, 0, 0, 0}
+// (error-bound coefficients errP0, errGx, errGy; the static terms errQ are
+// summed into Seg32::q_tot)
 // errP0 * (Theta + |cx| + |cy|) is the translation-error coefficient of the
 // running bound (Theta = largest |node coordinate| of the grid; node
 // coordinates are rounded once from FP64).
