@@ -443,6 +443,7 @@ def extra_hff(lt, W, torch, dev, steps=3):
     n = w.grids[0].nx
     m = lt.Model(w.n_pot, 1)
     m.set_params(w.params)
+    shape = m.autotune(grid)
     a32 = torch.empty((n, n, 2), dtype=torch.float32, device=dev)
 
     def time_it(fn, k):
@@ -465,7 +466,7 @@ def extra_hff(lt, W, torch, dev, steps=3):
     npot = w.grids[0].nodes * w.n_pot
     return {"workload": "6730^2 pixels at 0.03\", 2 cluster + 700 galaxy SIE (Sect. 4)",
             "node_pot": npot, "fp32_s": t32, "fp64_s": t64, "paper_mixed_s": t_paper,
-            "paper_mixed_fp64_nodes": stats["fp64_nodes"],
+            "paper_mixed_fp64_nodes": stats["fp64_nodes"], "deflect_shape": shape,
             "fp32_node_pot_per_s": npot / t32, "fp64_node_pot_per_s": npot / t64,
             "paper_s": {"V100": {"dp": 0.46, "mixed": 0.39}, "P100": {"dp": 0.71, "mixed": 0.58},
                         "GTX1080Ti": {"dp": 6.8, "mixed": 1.58}, "Xeon12c": {"dp": 8.1, "mixed": 7.40}},
@@ -542,13 +543,14 @@ def extra_large(lt, W, torch, dev, steps=2):
     grid = [w.grids[0].as_tuple()]
     m = lt.Model(w.n_pot, 1, hit_capacity=1 << 17)
     m.set_params(w.params)
+    shape = m.autotune(grid[0])
     obs = lt.Observations.from_dict(o, device=dev)
     t_val = _time(lambda: m.chi2(grid, obs, precision=lt.MIXED), torch, steps)
     t_grad = _time(lambda: m.chi2_grad(grid, obs, precision=lt.MIXED), torch, steps)
     st, stats = m.sync()
     m.close()
     return {"workload": "c5: 1000 PIEMD, 4000^2 grid, 100 systems, one sample",
-            "chi2_s": t_val, "chi2_grad_s": t_grad,
+            "chi2_s": t_val, "chi2_grad_s": t_grad, "deflect_shape": shape,
             "node_pot_per_s": w.grids[0].nx * w.grids[0].ny * w.n_pot / t_val,
             "status": int(st), "stats": stats}
 

@@ -210,10 +210,12 @@ SampleGrid sample_grid(const lt_grid& g, int64_t node_off) {
   return s;
 }
 
-int64_t defl_item_nodes(int precision, int shape) {
-  if (precision == LT_PREC_FP64) return kDefl64Nodes;
-  DeflectShape sh = deflect_shape(shape);
-  return (int64_t)sh.threads * sh.npt;
+// Deflection work items of one grid: node ranges of kDefl64Nodes in FP64,
+// column bands of the launch shape in FP32 (defl32_items).
+int64_t defl_items(const lt_grid& g, int precision, int shape) {
+  if (precision == LT_PREC_FP64) return ((int64_t)g.nx * g.ny + kDefl64Nodes - 1) / kDefl64Nodes;
+  const DeflectShape sh = deflect_shape(shape);
+  return defl32_items(g.nx, g.ny, sh.threads, sh.npt);
 }
 
 // Group samples into chunks whose node workspace fits the budget, build each
@@ -227,7 +229,6 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
     LT_CHECK_ARG(grid_ok(grids[b]), "invalid grid (need nx, ny >= 1, dx, dy > 0, finite)");
   const size_t node_bytes = precision == LT_PREC_FP64 ? sizeof(double2) : sizeof(float4);
   const size_t budget_nodes = std::max<size_t>(m->ws_budget / node_bytes, 1);
-  const int64_t dn = defl_item_nodes(precision, shape);
   const int64_t sc = precision == LT_PREC_FP64 ? kSearch64Cells : kSearch32Cells;
   Plan p;
   p.grids.assign(grids, grids + n);
@@ -254,7 +255,7 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
     int64_t acc = 0;
     for (int k = c.b0; k < c.b1; ++k) {
       items.push_back(acc);
-      acc += ((int64_t)grids[k].nx * grids[k].ny + dn - 1) / dn;
+      acc += defl_items(grids[k], precision, shape);
     }
     items.push_back(acc);
     c.defl_items = acc;
@@ -622,9 +623,8 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   const int64_t nodes = (int64_t)g.nx * g.ny;
   LT_CHECK_ARG(precision != LT_PREC_PAPER || nodes < ((int64_t)1 << 31),
                "LT_PREC_PAPER grids are limited to 2^31 nodes");
-  const int64_t dn = defl_item_nodes(precision == LT_PREC_FP64 ? LT_PREC_FP64 : LT_PREC_MIXED,
-                                     m->shape);
-  int64_t items[2] = {0, (nodes + dn - 1) / dn};
+  int64_t items[2] = {
+      0, defl_items(g, precision == LT_PREC_FP64 ? LT_PREC_FP64 : LT_PREC_MIXED, m->shape)};
   static_assert(sizeof(SampleGrid) % 8 == 0, "alignment");
   struct OneSample {
     SampleGrid g;
@@ -932,9 +932,7 @@ lt_status lt_autotune(lt_model* m, const lt_grid* grid, uintptr_t stream, int32_
   static_assert(sizeof(OneShape) % 8 == 0, "alignment");
   std::vector<OneShape> hs(kNumShapes);
   for (int v = 0; v < kNumShapes; ++v) {
-    const DeflectShape sh = deflect_shape(v);
-    const int64_t dn = (int64_t)sh.threads * sh.npt;
-    hs[v] = OneShape{sample_grid(g, 0), {0, (nodes + dn - 1) / dn}};
+    hs[v] = OneShape{sample_grid(g, 0), {0, defl_items(g, LT_PREC_MIXED, v)}};
   }
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t node_bytes = up(sizeof(float4) * (size_t)nodes);

@@ -13,8 +13,10 @@ namespace lt {
 constexpr int kChunk32 = 256;  // potentials staged in shared memory at a time
 
 // --------------------------------------------------------------- deflection
-template <int NT, int NPT>
-__global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot32,
+// MINB: the resident blocks per SM the register allocation must allow (left
+// to the compiler, the (256, 4) shape is squeezed into 64 registers and spills)
+template <int NT, int NPT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict__ pot32,
                                                   const Seg32* __restrict__ seg, int n_pot,
                                                   const SampleGrid* __restrict__ grids,
                                                   const int64_t* __restrict__ item_off,
@@ -34,19 +36,21 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
     int b = find_sample(item_off, n_samples, item);
     const SampleGrid g = grids[b];
     const Seg32 sg = seg[b];
-    const int64_t nodes = (int64_t)g.nx * g.ny;
-    const int64_t base = (item - item_off[b]) * (int64_t)(NT * NPT);
-        float X[NPT], Y[NPT], AX[NPT], AY[NPT], ER[NPT];
+    // this thread's column i and rows j0 .. j0 + NPT - 1 (see defl32_items)
+    const int64_t bands = ((int64_t)g.ny + NPT - 1) / NPT;
+    const int64_t p = (item - item_off[b]) * NT + threadIdx.x;
+    const bool live = p < bands * g.nx;
+    const int64_t pc = live ? p : 0;
+    const int band = (int)(pc / g.nx);
+    const int i = (int)(pc - (int64_t)band * g.nx);
+    const int j0 = band * NPT;
+    // node coordinates rounded once from FP64: error u|theta| (App. A's
+    // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
+    const float X = (float)(g.x0 + (double)i * g.dx);
+    float Y[NPT], AX[NPT], AY[NPT], ER[NPT];
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
-      int64_t n = base + m * NT + threadIdx.x;
-      if (n >= nodes) n = nodes - 1;
-      int j = (int)(n / g.nx);
-      int i = (int)(n - (int64_t)j * g.nx);
-      // node coordinates rounded once from FP64: error u|theta| (App. A's
-      // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
-      X[m] = (float)(g.x0 + (double)i * g.dx);
-      Y[m] = (float)(g.y0 + (double)j * g.dy);
+      Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
       AX[m] = 0.0f;
       AY[m] = 0.0f;
       ER[m] = 0.0f;
@@ -73,9 +77,7 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
       const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
       for (int k = 0; k < e_sis; ++k) {
         const float4* f = &sp[k * 5];
-        const float P = f[4].x;
-#pragma unroll
-        for (int m = 0; m < NPT; ++m) sis32(f, P, X[m], Y[m], AX[m], AY[m], ER[m]);
+        sis32_nodes<NPT>(f, f[4].x, X, Y, AX, AY, ER);
       }
       for (int k = e_sis; k < e_pie; ++k) {
         const float4* f = &sp[k * 5];
@@ -83,55 +85,69 @@ __global__ void __launch_bounds__(NT) k_deflect32(const Pot32* __restrict__ pot3
       }
       for (int k = e_pie; k < cn; ++k) {
         const float4* f = &sp[k * 5];
-        const float P = f[4].x;
-#pragma unroll
-        for (int m = 0; m < NPT; ++m) sie32(f, P, X[m], Y[m], AX[m], AY[m], ER[m]);
+        sie32_nodes<NPT>(f, f[4].x, X, Y, AX, AY, ER);
       }
     }
     const float qs = sg.q_tot;
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
-      int64_t n = base + m * NT + threadIdx.x;
-      if (n < nodes)
-        node_out[g.node_off + n] =
+      if (live && j0 + m < g.ny)
+        node_out[g.node_off + (int64_t)(j0 + m) * g.nx + i] =
             make_float4(AX[m], AY[m], node_bound(ER[m] + qs), 0.0f);
     }
   }
 }
 
-template <int NT, int NPT>
+template <int NT, int NPT, int MINB>
 static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int n_pot,
                                       const SampleGrid* grids, const int64_t* item_off,
                                       int n_samples, int64_t n_items, float4* node_out,
                                       unsigned long long* next_item, int sm_count,
                                       cudaStream_t st) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32<NT, NPT>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32<NT, NPT, MINB>, NT, 0);
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)sm_count * per_sm;
   if (blocks > n_items) blocks = n_items;
   if (blocks < 1) return cudaSuccess;
-  k_deflect32<NT, NPT><<<(unsigned)blocks, NT, 0, st>>>(pot32, seg, n_pot, grids, item_off,
+  k_deflect32<NT, NPT, MINB><<<(unsigned)blocks, NT, 0, st>>>(pot32, seg, n_pot, grids, item_off,
                                                           n_samples, n_items, node_out,
                                                           next_item);
   return cudaGetLastError();
+}
+
+template <int V>
+static cudaError_t launch_shape(const Pot32* pot32, const Seg32* seg, int n_pot,
+                               const SampleGrid* grids, const int64_t* item_off, int n_samples,
+                               int64_t n_items, float4* node_out, unsigned long long* next_item,
+                               int sm_count, cudaStream_t st) {
+  constexpr DeflectShape sh = deflect_shape(V);
+  return launch_deflect32_t<sh.threads, sh.npt, sh.min_blocks>(
+      pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item, sm_count, st);
 }
 
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
                              const SampleGrid* grids, const int64_t* item_off, int n_samples,
                              int64_t n_items, int shape, float4* node_out,
                              unsigned long long* next_item, int sm_count, cudaStream_t st) {
+  static_assert(kNumShapes == 8, "one case per launch shape");
   switch (shape) {
-    case 1: return launch_deflect32_t<256, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    case 2: return launch_deflect32_t<512, 2>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    case 3: return launch_deflect32_t<128, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    case 4: return launch_deflect32_t<128, 8>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                              n_items, node_out, next_item, sm_count, st);
-    default: return launch_deflect32_t<256, 4>(pot32, seg, n_pot, grids, item_off, n_samples,
-                                               n_items, node_out, next_item, sm_count, st);
+    case 1: return launch_shape<1>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    case 2: return launch_shape<2>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    case 3: return launch_shape<3>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    case 4: return launch_shape<4>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    case 5: return launch_shape<5>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    case 6: return launch_shape<6>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    case 7: return launch_shape<7>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                   node_out, next_item, sm_count, st);
+    default: return launch_shape<0>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
+                                    node_out, next_item, sm_count, st);
   }
 }
 

@@ -6,21 +6,35 @@
 
 namespace lt {
 
+// The node set of one thread: NPT nodes of one grid column, at X and at the
+// rows Y[0..NPT-1].  The translation dx = X - c_x and its products with the
+// rotation coefficients are formed once per potential and shared by the NPT
+// nodes; each node then needs dy = Y - c_y and one fma per rotated component.
+// Which of the two products of a rotated component is rounded separately
+// (dx c or dy s) does not change its error bound: both are at most the
+// distance times the coefficient.
+
 // One SIS: alpha += b0 (theta - c)/R (zero at the centre).  err accumulates in
 // units of the FP32 unit roundoff.
-__device__ __forceinline__ void sis32(const float4* f, float P, float x, float y, float& ax,
-                                      float& ay, float& err) {
-  float dx = x - f[0].x, dy = y - f[0].y;
-  float R2 = fmaf(dx, dx, dy * dy);
-  // rr is +inf on the centre: there the direction of alpha is undefined and
-  // the bound term P rr makes the node's bound infinite (never certified)
-  const float rr = rsqrtf(R2);
-  const float ri = R2 > 0.0f ? rr : 0.0f;
-  float g = f[0].z * ri;
-  ax = fmaf(g, dx, ax);
-  ay = fmaf(g, dy, ay);
-  err = fmaf(P, rr, err);
-  err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
+template <int NPT>
+__device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, const float* Y,
+                                            float* AX, float* AY, float* ER) {
+  const float dx = X - f[0].x;
+  const float dx2 = dx * dx;
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    const float dy = Y[m] - f[0].y;
+    const float R2 = fmaf(dy, dy, dx2);
+    // rr is +inf on the centre: there the direction of alpha is undefined and
+    // the bound term P rr makes the node's bound infinite (never certified)
+    const float rr = rsqrtf(R2);
+    const float ri = R2 > 0.0f ? rr : 0.0f;
+    const float g = f[0].z * ri;
+    AX[m] = fmaf(g, dx, AX[m]);
+    AY[m] = fmaf(g, dy, AY[m]);
+    ER[m] = fmaf(P, rr, ER[m]);
+    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+  }
 }
 
 // One SIE (Algorithm 1), with the axis weights folded into the rotation:
@@ -33,20 +47,26 @@ __device__ __forceinline__ void sis32(const float4* f, float P, float x, float y
 // f[0] = {cx, cy, sqrt(1-eps) c, sqrt(1-eps) s},
 // f[1] = {sqrt(1+eps) c, sqrt(1+eps) s, b0 sqrt(1-eps) c, b0 sqrt(1+eps) s},
 // f[2] = {b0 sqrt(1+eps) c, b0 sqrt(1-eps) s, 0, 0}.
-__device__ __forceinline__ void sie32(const float4* f, float P, float x, float y, float& ax,
-                                      float& ay, float& err) {
-  const float dx = x - f[0].x, dy = y - f[0].y;
-  const float u = fmaf(dx, f[0].z, dy * f[0].w);
-  const float v = fmaf(dy, f[1].x, -(dx * f[1].y));
-  const float R2 = fmaf(u, u, v * v);
-  const float rr = rsqrtf(R2);  // +inf on the centre: an infinite bound there
-  const float ri = R2 > 0.0f ? rr : 0.0f;
-  const float t1 = fmaf(f[1].z, u, -(f[1].w * v));
-  const float t2 = fmaf(f[2].x, v, f[2].y * u);
-  ax = fmaf(ri, t1, ax);
-  ay = fmaf(ri, t2, ay);
-  err = fmaf(P, rr, err);
-  err = fmaf(2.0f, fabsf(ax) + fabsf(ay), err);
+template <int NPT>
+__device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, const float* Y,
+                                            float* AX, float* AY, float* ER) {
+  const float dx = X - f[0].x;
+  const float dxu = dx * f[0].z, dxv = dx * f[1].y;
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    const float dy = Y[m] - f[0].y;
+    const float u = fmaf(dy, f[0].w, dxu);
+    const float v = fmaf(dy, f[1].x, -dxv);
+    const float R2 = fmaf(u, u, v * v);
+    const float rr = rsqrtf(R2);  // +inf on the centre: an infinite bound there
+    const float ri = R2 > 0.0f ? rr : 0.0f;
+    const float t1 = fmaf(f[1].z, u, -(f[1].w * v));
+    const float t2 = fmaf(f[2].x, v, f[2].y * u);
+    AX[m] = fmaf(ri, t1, AX[m]);
+    AY[m] = fmaf(ri, t2, AY[m]);
+    ER[m] = fmaf(P, rr, ER[m]);
+    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+  }
 }
 
 // One PIEMD (dPIE) in difference form.  With psi_w = sqrt(q^2(w^2+x'^2)+y'^2),
@@ -58,26 +78,28 @@ __device__ __forceinline__ void sie32(const float4* f, float P, float x, float y
 // psi_s - psi_a = q^2 (s^2-a^2)/(psi_a+psi_s)), which avoids the cancellation
 // of the two cored terms and halves the transcendental work.
 //
-// One PIEMD on the NPT nodes of a thread.  The range tests of the two special
-// functions are merged into one branch per thread and potential: both
-// polynomials of atanc_sq32 / atanhc_sq32 are evaluated on the unreduced
+// One PIEMD on the NPT nodes of a thread (one column).  The range tests of
+// the two special functions are merged into one branch per thread and
+// potential: both polynomials of atanc_sq32 / atanhc_sq32 are evaluated on the unreduced
 // arguments for every node (finite for any argument), and the nodes outside
 // their ranges (atan: t2 > 1, atanh: t2 > 0.25; about 14 % of node-potential
 // pairs on cluster lenses) are then recomputed by those functions.  Every node
 // gets exactly the values and roundings of the per-node evaluation; the
 // merged test removes most of the branch instructions from the issue stream.
 template <int NPT>
-__device__ __forceinline__ void piemd32_nodes(const float4* f, float P, const float* X,
-                                              const float* Y, float* AX, float* AY, float* ER) {
-  const float cx = f[0].x, cy = f[0].y, c = f[0].z, s = f[0].w;
+__device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X, const float* Y,
+                                              float* AX, float* AY, float* ER) {
+  const float cy = f[0].y, c = f[0].z, s = f[0].w;
   const float k2 = f[1].w, Bc = f[3].w, Bs = f[4].w;
+  const float dx = X - f[0].x;
+  const float dxc = dx * c, dxs = dx * s;
   float tx[NPT], ty[NPT], ux[NPT], uy[NPT], ra[NPT], px_[NPT], py_[NPT];
   bool any = false;
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
-    const float dx = X[m] - cx, dy = Y[m] - cy;
-    const float xp = fmaf(dx, c, dy * s);
-    const float yp = fmaf(dy, c, -(dx * s));
+    const float dy = Y[m] - cy;
+    const float xp = fmaf(dy, s, dxc);
+    const float yp = fmaf(dy, c, -dxs);
     const float x2 = xp * xp, y2 = yp * yp;
     const float t = fmaf(f[1].x, x2, y2);
     const float pa2 = t + f[1].y, ps2 = t + f[1].z;

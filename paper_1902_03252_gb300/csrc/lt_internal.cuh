@@ -238,13 +238,24 @@ __device__ __forceinline__ float atanhc_sq32(float t2) {
 
 // Launch-shape variants of the FP32 deflection kernel (autotuned).
 struct DeflectShape {
-  int threads;  // threads per block
-  int npt;      // nodes per thread
+  int threads;     // threads per block
+  int npt;         // nodes per thread (rows of one column)
+  int min_blocks;  // resident blocks per SM the register budget must allow
 };
-constexpr int kNumShapes = 5;
-__host__ __device__ inline DeflectShape deflect_shape(int v) {
-  const DeflectShape tab[kNumShapes] = {{256, 4}, {256, 2}, {512, 2}, {128, 4}, {128, 8}};
+constexpr int kNumShapes = 8;
+__host__ __device__ constexpr DeflectShape deflect_shape(int v) {
+  const DeflectShape tab[kNumShapes] = {{128, 4, 7}, {256, 2, 5}, {256, 3, 4}, {128, 8, 3},
+                                        {128, 8, 4}, {256, 4, 3}, {128, 4, 8}, {256, 2, 6}};
   return tab[v < 0 || v >= kNumShapes ? 0 : v];
+}
+
+// Work items of the FP32 deflection.  A thread takes npt nodes of one grid
+// column: rows [band*npt, band*npt + npt) of band `band`.  A sample's
+// (band, column) positions, band-major, are cut into items of `threads`
+// consecutive positions; only the last band of a sample can be partly empty.
+__host__ __device__ inline int64_t defl32_items(int nx, int ny, int threads, int npt) {
+  const int64_t bands = ((int64_t)ny + npt - 1) / npt;
+  return (bands * nx + threads - 1) / threads;
 }
 
 // ----------------------------------------------------------- batch layout

@@ -57,32 +57,36 @@ lt_status device_setup(int dev, unsigned char** base, int* sms) {
   return LT_OK;
 }
 
-constexpr int kNT = 256, kNPT = 4;
+// the default launch shape of the batched kernel: 128 threads, 4 rows each,
+// registers for 7 resident blocks per SM
+constexpr int kNT = 128, kNPT = 4, kMinBlocks = 7;
 
 // Same arithmetic as the batched deflection kernel (same per-potential
 // functions, kind segments and order), for one sample, writing alpha and the
 // running error bound straight into the caller's buffers.
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kNT, kMinBlocks)
     k_deflect32_noalloc(const Pot32* __restrict__ pot32, const Seg32* __restrict__ seg, int n_pot,
                         SampleGrid g, int64_t n_items, float2* __restrict__ alpha,
                         float* __restrict__ err) {
   __shared__ float4 sp[256 * 5];
   const Seg32 sg = *seg;
-  const int64_t nodes = (int64_t)g.nx * g.ny;
+  const int64_t bands = ((int64_t)g.ny + kNPT - 1) / kNPT;
   const float theta1 = g.theta_max;
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int64_t base = item * (int64_t)(kNT * kNPT);
-    float X[kNPT], Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
+    // this thread's column i and rows j0 .. j0 + kNPT - 1 (see defl32_items)
+    const int64_t p = item * kNT + threadIdx.x;
+    const bool live = p < bands * g.nx;
+    const int64_t pc = live ? p : 0;
+    const int band = (int)(pc / g.nx);
+    const int i = (int)(pc - (int64_t)band * g.nx);
+    const int j0 = band * kNPT;
+    // node coordinates rounded once from FP64: error u|theta| (App. A's
+    // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
+    const float X = (float)(g.x0 + (double)i * g.dx);
+    float Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {
-      int64_t n = base + m * kNT + threadIdx.x;
-      if (n >= nodes) n = nodes - 1;
-      const int j = (int)(n / g.nx);
-      const int i = (int)(n - (int64_t)j * g.nx);
-      // node coordinates rounded once from FP64: error u|theta| (App. A's
-      // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
-      X[m] = (float)(g.x0 + (double)i * g.dx);
-      Y[m] = (float)(g.y0 + (double)j * g.dy);
+      Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
       AX[m] = 0.0f;
       AY[m] = 0.0f;
       ER[m] = 0.0f;
@@ -104,23 +108,17 @@ __global__ void __launch_bounds__(kNT)
       __syncthreads();
       const int e_sis = min(max(sg.n_sis - c0, 0), cn);
       const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
-      for (int k = 0; k < e_sis; ++k) {
-#pragma unroll
-        for (int m = 0; m < kNPT; ++m) sis32(&sp[k * 5], sp[k * 5 + 4].x, X[m], Y[m], AX[m], AY[m], ER[m]);
-      }
-      for (int k = e_sis; k < e_pie; ++k) {
-#pragma unroll
+      for (int k = 0; k < e_sis; ++k)
+        sis32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
+      for (int k = e_sis; k < e_pie; ++k)
         piemd32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
-      }
-      for (int k = e_pie; k < cn; ++k) {
-#pragma unroll
-        for (int m = 0; m < kNPT; ++m) sie32(&sp[k * 5], sp[k * 5 + 4].x, X[m], Y[m], AX[m], AY[m], ER[m]);
-      }
+      for (int k = e_pie; k < cn; ++k)
+        sie32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
     }
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {
-      const int64_t n = base + m * kNT + threadIdx.x;
-      if (n < nodes) {
+      if (live && j0 + m < g.ny) {
+        const int64_t n = (int64_t)(j0 + m) * g.nx + i;
         alpha[n] = make_float2(AX[m], AY[m]);
         if (err) err[n] = node_bound(ER[m] + sg.q_tot);
       }
@@ -169,8 +167,7 @@ extern "C" lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot
   g.theta_max = (float)(tm * (1.0 + 1e-6));
   g.pad = 0.f;
   g.x0f = (float)gr.x0; g.y0f = (float)gr.y0; g.dxf = (float)gr.dx; g.dyf = (float)gr.dy;
-  const int64_t nodes = (int64_t)gr.nx * gr.ny;
-  const int64_t n_items = (nodes + kNT * kNPT - 1) / (kNT * kNPT);
+  const int64_t n_items = defl32_items(gr.nx, gr.ny, kNT, kNPT);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32_noalloc, kNT, 0) !=
       cudaSuccess)

@@ -141,7 +141,7 @@ def test_deflect_bound_adversarial(oracle):
     m.close()
 
 
-@pytest.mark.parametrize("shape", range(5))
+@pytest.mark.parametrize("shape", range(8))
 def test_deflect_every_shape_within_bound(oracle, shape):
     """Every launch shape of the FP32 deflection on 300 potentials of all
     three kinds -- more than one staged chunk of 256 -- over a grid whose node
@@ -154,6 +154,7 @@ def test_deflect_every_shape_within_bound(oracle, shape):
     p[3, 2::5] = rng.uniform(0, 0.3, p[3, 2::5].shape)
     grid = (-45.0, -41.0, 90.0 / 250, 82.0 / 231, 251, 232)
     m = lt.Model(p.shape[1], 1)
+    assert m._lib.lt_num_shapes() == 8
     m.set_params(p[None])
     m.set_shape(shape)
     a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
