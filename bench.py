@@ -416,8 +416,9 @@ def run_ours(a, rank, world, local):
                 "h2d_bytes_per_step": int(host_params.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8), "ms_per_step": e2e_ms},
         "clocks": clk,
-        # kernels of the chi^2 stages (counted by the library) + k_prep per step
-        "gpu_launches": int(round((launches_per_step + 1) * a.steps)),
+        # kernels of the chi^2 stages (counted by the library) + k_prep and
+        # the counter reset (k_zero64) per step
+        "gpu_launches": int(round((launches_per_step + 2) * a.steps)),
         "wall_s_timed_region": wall,
         "deflect32_source_sha256": source_sha(DEFLECT32_SOURCES),
     }

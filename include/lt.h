@@ -157,9 +157,10 @@ const char* lt_status_string(lt_status status);
  *      SIE: pseudo-ellipticity eps, 0 <= eps < 1), phi (rad, major axis
  *   counter-clockwise from the x axis), r_core, r_cut (PIEMD only,
  *   0 < r_core < r_cut, arcsec), sigma_v (km/s, >= 0).
- * on_device != 0: params is a device pointer, else a host pointer (copied
- * asynchronously; the host buffer must stay valid until the stream reaches
- * the copy).  Invalid or non-finite values are latched as LT_ERR_NONFINITE
+ * on_device != 0: params is a device pointer, read in place by the
+ * preparation kernel (it must stay valid and unchanged until the stream
+ * reaches that kernel); else a host pointer (copied asynchronously; the host
+ * buffer must stay valid until the stream reaches the copy).  Invalid or non-finite values are latched as LT_ERR_NONFINITE
  * (reported by lt_model_sync). */
 lt_status lt_model_set_params(lt_model* model, const double* params, int on_device,
                               uintptr_t stream);

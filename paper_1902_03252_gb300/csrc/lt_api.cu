@@ -359,9 +359,14 @@ lt_status ensure_resolve(lt_model* m) {
     LT_CUDA(cudaMalloc(&m->rs.keys, sizeof(unsigned long long) * cap));
     LT_CUDA(cudaMalloc(&m->rs.hval, sizeof(double2) * cap));
     LT_CUDA(cudaMalloc(&m->rs.ulist, sizeof(int32_t) * cap));
+    // empty once here; every resolution leaves it empty again (k_res_tri)
+    LT_CUDA(cudaMemset(m->rs.keys, 0xff, sizeof(unsigned long long) * cap));
     m->rs.cap = cap;
   }
-  if (!m->rs.n_unique) LT_CUDA(cudaMalloc(&m->rs.n_unique, sizeof(unsigned int)));
+  if (!m->rs.n_unique) {
+    LT_CUDA(cudaMalloc(&m->rs.n_unique, sizeof(unsigned int)));
+    LT_CUDA(cudaMemset(m->rs.n_unique, 0, sizeof(unsigned int)));
+  }
   if (vslots > m->rs_vslot_alloc) {
     ++m->ws_epoch;
     if (m->rs.vslot) LT_CUDA(cudaFree(m->rs.vslot));
@@ -431,18 +436,21 @@ lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int
                               m->sm_count, st));
     }
     ProfScope ps(m, st, 2, 0.0, 0, 3);  // k_res_insert, k_res_nodes, k_res_tri
-    LT_CUDA(launch_resolve64(m->d_pot64, m->n_pot, g, src, work, wc, nb, m->work_cap, hits,
-                             hit_cap, hc, m->d_counters, m->d_status, m->rs, m->sm_count, st));
+    const cudaError_t re =
+        launch_resolve64(m->d_pot64, m->n_pot, g, src, work, wc, nb, m->work_cap, hits, hit_cap,
+                         hc, m->d_counters, m->d_status, m->rs, m->sm_count, st);
+    // a failed launch may leave the table partly filled: reallocate (and so
+    // clear) it on the next call
+    if (re != cudaSuccess) m->rs.cap = 0;
+    LT_CUDA(re);
   }
   return LT_OK;
 }
 
 lt_status reset_counts(lt_model* m, cudaStream_t st) {
-  LT_CUDA(cudaMemsetAsync(m->d_counters, 0, sizeof(long long) * CNT_N, st));
-  if (m->d_sched)
-    LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long) * m->sched_alloc, st));
-  LT_CUDA(cudaMemsetAsync(m->d_hit_count, 0, sizeof(unsigned long long) * m->batch, st));
-  LT_CUDA(cudaMemsetAsync(m->d_work_count, 0, sizeof(unsigned long long) * m->batch, st));
+  LT_CUDA(launch_zero64((unsigned long long*)m->d_counters, CNT_N, m->d_sched,
+                        (int64_t)m->sched_alloc, m->d_hit_count, m->batch, m->d_work_count,
+                        m->batch, st));
   return LT_OK;
 }
 
@@ -596,11 +604,15 @@ lt_status lt_model_set_params(lt_model* m, const double* params, int on_device,
   if (!m) return LT_ERR_INVALID_ARG;
   LT_CHECK_ARG(params != nullptr, "params is NULL");
   const size_t bytes = sizeof(double) * LT_N_ROWS * (size_t)m->n_pot * m->batch;
-  LT_CUDA(cudaMemcpyAsync(m->d_params, params, bytes,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          S(stream)));
-  LT_CUDA(launch_prep(m->d_params, m->batch, m->n_pot, m->d_pot64, m->d_pot32, m->d_seg,
-                      m->d_status, S(stream)));
+  // device parameters are read in place by the preparation kernel (stream
+  // ordered, like a copy would be); host parameters are uploaded first
+  const double* src = params;
+  if (!on_device) {
+    LT_CUDA(cudaMemcpyAsync(m->d_params, params, bytes, cudaMemcpyHostToDevice, S(stream)));
+    src = m->d_params;
+  }
+  LT_CUDA(launch_prep(src, m->batch, m->n_pot, m->d_pot64, m->d_pot32, m->d_seg, m->d_status,
+                      S(stream)));
   return LT_OK;
 }
 

@@ -175,6 +175,37 @@ __global__ void __launch_bounds__(kPrepThreads)
   }
 }
 
+__global__ void k_zero64(unsigned long long* a, int64_t na, unsigned long long* b, int64_t nb,
+                         unsigned long long* c, int64_t nc, unsigned long long* d, int64_t nd) {
+  const int64_t n = na + nb + nc + nd;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = i;
+    if (k < na) { a[k] = 0ull; continue; }
+    k -= na;
+    if (k < nb) { b[k] = 0ull; continue; }
+    k -= nb;
+    if (k < nc) { c[k] = 0ull; continue; }
+    k -= nc;
+    d[k] = 0ull;
+  }
+}
+
+cudaError_t launch_zero64(unsigned long long* a, int64_t na, unsigned long long* b, int64_t nb,
+                          unsigned long long* c, int64_t nc, unsigned long long* d, int64_t nd,
+                          cudaStream_t st) {
+  if (!a) na = 0;
+  if (!b) nb = 0;
+  if (!c) nc = 0;
+  if (!d) nd = 0;
+  const int64_t n = na + nb + nc + nd;
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_zero64<<<(unsigned)blocks, 256, 0, st>>>(a, na, b, nb, c, nc, d, nd);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,
                         Seg32* seg, uint32_t* status, cudaStream_t st) {
   k_prep<<<batch, kPrepThreads, 0, st>>>(params, n_pot, pot64, pot32, seg, status);
@@ -486,7 +517,11 @@ __global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
                           int64_t work_cap, const int32_t* __restrict__ vslot,
                           const double2* __restrict__ hval, Hit* __restrict__ hits,
                           int64_t hit_cap, unsigned long long* hit_count, long long* counters,
-                          uint32_t* status) {
+                          uint32_t* status, unsigned long long* __restrict__ keys,
+                          unsigned int* __restrict__ n_unique) {
+  // this kernel is the table's last reader: it leaves the table empty for the
+  // next call (the distinct-node list count here, every used slot below)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_unique = 0u;
   long long n_hit = 0;
   const int64_t total = (int64_t)n_samples * work_cap;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total;
@@ -496,6 +531,11 @@ __global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
     const unsigned long long cnt = work_count[b];
     if ((unsigned long long)idx >= (cnt < (unsigned long long)work_cap ? cnt : work_cap)) continue;
     const Work64 wk = work[f];
+    // several items may share a slot: they all write the same value
+    for (int v = 0; v < 3; ++v) {
+      const int32_t slot = vslot[f * 3 + v];
+      if (slot >= 0) keys[slot] = kEmptyKey;
+    }
     const SampleGrid g = grids[b];
     const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
     const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
@@ -545,10 +585,8 @@ cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* gr
   unsigned long long cap = 1024;
   while (cap < 6ull * (unsigned long long)n_samples * (unsigned long long)work_cap) cap <<= 1;
   if (cap > rs.cap) return cudaErrorInvalidValue;  // sized by the caller from the same formula
-  cudaError_t e = cudaMemsetAsync(rs.keys, 0xff, sizeof(unsigned long long) * cap, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(rs.n_unique, 0, sizeof(unsigned int), st);
-  if (e != cudaSuccess) return e;
+  // the table (all keys empty, no distinct nodes) is cleared once at
+  // allocation and left empty again by k_res_tri
   const int64_t slots3 = (int64_t)n_samples * work_cap * 3;
   int64_t b1 = (slots3 + 255) / 256;
   if (b1 > (int64_t)sm_count * 16) b1 = (int64_t)sm_count * 16;
@@ -561,7 +599,7 @@ cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* gr
   if (b3 > (int64_t)sm_count * 16) b3 = (int64_t)sm_count * 16;
   k_res_tri<<<(unsigned)b3, 128, 0, st>>>(grids, src, work, work_count, n_samples, work_cap,
                                            rs.vslot, rs.hval, hits, hit_cap, hit_count, counters,
-                                           status);
+                                           status, rs.keys, rs.n_unique);
   return cudaGetLastError();
 }
 

@@ -303,6 +303,11 @@ __device__ __forceinline__ int find_sample(const int64_t* off, int n, int64_t it
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the cudaGetLastError() value.
+// Zero up to four arrays of 64-bit counters in one launch (the per-call
+// counter resets of a chi^2 evaluation: one kernel instead of four memsets).
+cudaError_t launch_zero64(unsigned long long* a, int64_t na, unsigned long long* b, int64_t nb,
+                          unsigned long long* c, int64_t nc, unsigned long long* d, int64_t nd,
+                          cudaStream_t st);
 cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,
                         Seg32* seg, uint32_t* status, cudaStream_t st);
 // next_item: a zeroed device counter, taken by atomicAdd (dynamic items)
