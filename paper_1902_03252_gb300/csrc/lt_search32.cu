@@ -155,12 +155,14 @@ __global__ void __launch_bounds__(kSearchThreads, 6)
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   long long n_hit = 0, n_amb = 0, n_ref = 0;
   int staged = -1;  // sample whose whole source list is in ss (block-uniform)
+  int b = 0;        // sample of the previous item: the next one is usually in it
   // static distribution of the items: the search follows the deflection on
   // the same stream, so every block starts together and the fetch latency of
   // a shared counter would sit on each item's critical path
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
     __syncthreads();  // the previous item's readers of sb / surv are done
-    const int b = find_sample(item_off, n_samples, item);
+    if (n_samples > 1 && !(item_off[b] <= item && item < item_off[b + 1]))
+      b = find_sample(item_off, n_samples, item);
     const SampleGrid g = grids[b];
     const int sample = src.sample_base + b;
     const int64_t cells = (int64_t)(g.nx - 1) * (g.ny - 1);
