@@ -21,7 +21,6 @@ namespace {
 
 constexpr int64_t kDefaultCap = 4096;
 constexpr int kDefl64Nodes = 128;    // nodes per FP64 deflection item
-constexpr int kSearch32Cells = 128;  // cells per FP32 search item (= k_search32 block size)
 constexpr int kSearch64Cells = 128;  // cells per FP64 search item
 
 struct Chunk {
@@ -229,7 +228,6 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
     LT_CHECK_ARG(grid_ok(grids[b]), "invalid grid (need nx, ny >= 1, dx, dy > 0, finite)");
   const size_t node_bytes = precision == LT_PREC_FP64 ? sizeof(double2) : sizeof(float4);
   const size_t budget_nodes = std::max<size_t>(m->ws_budget / node_bytes, 1);
-  const int64_t sc = precision == LT_PREC_FP64 ? kSearch64Cells : kSearch32Cells;
   Plan p;
   p.grids.assign(grids, grids + n);
   p.precision = precision;
@@ -263,7 +261,10 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
     acc = 0;
     for (int k = c.b0; k < c.b1; ++k) {
       items.push_back(acc);
-      acc += ((int64_t)(grids[k].nx - 1) * (grids[k].ny - 1) + sc - 1) / sc;
+      acc += precision == LT_PREC_FP64
+                 ? ((int64_t)(grids[k].nx - 1) * (grids[k].ny - 1) + kSearch64Cells - 1) /
+                       kSearch64Cells
+                 : search32_items(grids[k].nx, grids[k].ny);
     }
     items.push_back(acc);
     c.search_items = acc;

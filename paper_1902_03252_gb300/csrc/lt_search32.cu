@@ -11,7 +11,7 @@
 namespace lt {
 
 // ---------------------------------------------------------- triangle search
-constexpr int kSearchThreads = 128;  // cells per work item (one per thread)
+constexpr int kSearchThreads = kSearch32Threads;  // positions per work item
 constexpr int kMaxSrcSmem = 256;     // sources staged in shared memory at a time
 
 // Source data staged per sample: position relative coordinates use FP32.
@@ -126,20 +126,59 @@ __device__ __noinline__ double2 hit_xy(double x0, double y0, double dx, double d
                       Y0 + (double)w1 * (Y1 - Y0) + (double)w2 * (Y1 - Y0));
 }
 
-// One work item = 128 consecutive cells, 4 warps of 32 ("strips").  For each
-// chunk of sources: (1) every (strip, source) pair is tested once, by one
-// thread, against a conservative source-plane box of the strip,
+// Emit the outcome of one cell's two triangles for the whole warp: certain
+// hits (interpolated in FP64 from the node coordinates) and the pairs that go
+// to the FP64 work list.  Every lane calls it (warp ballots inside).
+__device__ __forceinline__ void emit_cell(const SampleGrid& g, int sample, int b, int src_k,
+                                          int64_t cell, int i, int j, int r0, int r1,
+                                          const float* w0, const float* w1, bool ok0, bool ok1,
+                                          Hit* hits, int64_t hit_cap, Work64* work,
+                                          int64_t work_cap, unsigned long long* hit_count,
+                                          unsigned long long* work_count, uint32_t* status,
+                                          long long* counters) {
+  const bool wk0 = r0 == 2 || (r0 == 1 && !ok0);
+  const bool wk1 = r1 == 2 || (r1 == 1 && !ok1);
+  if (!__any_sync(0xffffffffu, ok0 || ok1 || wk0 || wk1)) return;
+  const int64_t tri0 = 2 * cell, tri1 = 2 * cell + 1;
+  Hit h;
+  h.src = src_k;
+  h.fp64 = 0;
+  h.tri = tri0;
+  h.w[0] = w0[0]; h.w[1] = w0[1]; h.w[2] = w0[2];
+  double2 xy = hit_xy(g.x0, g.y0, g.dx, g.dy, i, j, 0, w0[1], w0[2]);
+  h.x = xy.x;
+  h.y = xy.y;
+  Hit* hb = hits + (int64_t)b * hit_cap;
+  warp_append_hit(ok0, h, hb, hit_cap, hit_count + b, status);
+  h.tri = tri1;
+  h.w[0] = w1[0]; h.w[1] = w1[1]; h.w[2] = w1[2];
+  xy = hit_xy(g.x0, g.y0, g.dx, g.dy, i, j, 1, w1[1], w1[2]);
+  h.x = xy.x;
+  h.y = xy.y;
+  warp_append_hit(ok1, h, hb, hit_cap, hit_count + b, status);
+  Work64* wb = work + (int64_t)b * work_cap;
+  warp_append_work(wk0, Work64{sample, src_k, tri0, r0 == 2 ? 0 : 1, 0}, wb, work_cap,
+                   work_count + b, status, counters);
+  warp_append_work(wk1, Work64{sample, src_k, tri1, r1 == 2 ? 0 : 1, 0}, wb, work_cap,
+                   work_count + b, status, counters);
+}
+
+// One work item = 128 positions, 4 warps of 32 ("strips"); a position is two
+// vertically adjacent cells of one cell column (rows j and j + 1), which
+// share a row of nodes.  For each chunk of sources: (1) every (strip, source)
+// pair is tested once, by one thread, against a conservative source-plane box
+// of the strip,
 //   beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x]
 // (the same in y) widened by the strip's largest vertex uncertainty; the
 // surviving sources of each strip are compacted into a shared list; (2) each
 // warp runs the per-cell test only for its strip's survivors.  Most pairs
 // never reach the per-cell arithmetic.
 //
-// The kernel is latency-bound: blocks of 128 threads, six per SM (80
-// registers, a few bytes of spill), measure faster than fewer, larger blocks
-// or a spill-free register budget, as more independent barrier groups keep
-// the schedulers busy.
-__global__ void __launch_bounds__(kSearchThreads, 6)
+// The kernel is latency-bound (the per-item chain of loads, warp reductions
+// and barriers; its time barely changes between 1 and 20 sources): two cells
+// per thread halve the number of item iterations.  Four blocks per SM, with
+// the registers that allows, measure faster than five or six with spills.
+__global__ void __launch_bounds__(kSearchThreads, 4)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
                Hit* __restrict__ hits, int64_t hit_cap, Work64* __restrict__ work,
@@ -147,6 +186,7 @@ __global__ void __launch_bounds__(kSearchThreads, 6)
                long long* counters, uint32_t* status,
                unsigned long long* __restrict__ /*next_item: unused, static items*/) {
   constexpr int kStrips = kSearchThreads / 32;
+  static_assert(kSearch32Rows == 2, "the kernel handles two cell rows per thread");
   __shared__ SrcSmem ss[kMaxSrcSmem];
   __shared__ StripBox sb[kStrips];
   __shared__ unsigned short surv[kStrips][kMaxSrcSmem];
@@ -165,46 +205,65 @@ __global__ void __launch_bounds__(kSearchThreads, 6)
       b = find_sample(item_off, n_samples, item);
     const SampleGrid g = grids[b];
     const int sample = src.sample_base + b;
-    const int64_t cells = (int64_t)(g.nx - 1) * (g.ny - 1);
-    const int64_t cell = (item - item_off[b]) * kSearchThreads + threadIdx.x;
-    const bool valid = cell < cells;
-    const int64_t cl = valid ? cell : 0;
-    int i, j;
-    if (cells < ((int64_t)1 << 31)) {  // 32-bit index arithmetic
-      const unsigned c32 = (unsigned)cl, w32 = (unsigned)(g.nx - 1);
-      j = (int)(c32 / w32);
-      i = (int)(c32 - (unsigned)j * w32);
+    // this thread's cell column i and cell rows j, j + 1 (see search32_items)
+    const int cw = g.nx - 1, ch = g.ny - 1;
+    const int64_t npos = ((int64_t)ch + 1) / 2 * cw;
+    const int64_t p = (item - item_off[b]) * kSearchThreads + threadIdx.x;
+    const bool validA = p < npos;
+    const int64_t pc = validA ? p : 0;
+    int i, band;
+    if (npos < ((int64_t)1 << 31)) {  // 32-bit index arithmetic
+      const unsigned c32 = (unsigned)pc, w32 = (unsigned)cw;
+      band = (int)(c32 / w32);
+      i = (int)(c32 - (unsigned)band * w32);
     } else {
-      j = (int)(cl / (g.nx - 1));
-      i = (int)(cl - (int64_t)j * (g.nx - 1));
+      band = (int)(pc / cw);
+      i = (int)(pc - (int64_t)band * cw);
     }
+    const int j = 2 * band;
+    const bool validB = validA && j + 1 < ch;
     const int64_t n00 = g.node_off + (int64_t)j * g.nx + i;
+    // rows j, j + 1 and j + 2 (a copy of row j + 1 when there is no second cell)
+    const int64_t n02 = validB ? n00 + 2 * (int64_t)g.nx : n00 + g.nx;
     const float4 v00 = nodes[n00], v10 = nodes[n00 + 1], v01 = nodes[n00 + g.nx],
-                 v11 = nodes[n00 + g.nx + 1];
+                 v11 = nodes[n00 + g.nx + 1], v02 = nodes[n02], v12 = nodes[n02 + 1];
     const float hx = g.dxf, hy = g.dyf, gx0 = g.x0f, gy0 = g.y0f;
     const float hmax = fmaxf(fabsf(hx), fabsf(hy));
     const float xl = fmaf((float)i, hx, gx0);
     const float xr = fmaf((float)(i + 1), hx, gx0);
     const float yb = fmaf((float)j, hy, gy0);
-    const float yt = fmaf((float)(j + 1), hy, gy0);
-    const float emax = fmaxf(fmaxf(v00.z, v10.z), fmaxf(v01.z, v11.z));
-    const float l00 = fabsf(v00.x) + fabsf(v00.y), l10 = fabsf(v10.x) + fabsf(v10.y);
-    const float l01 = fabsf(v01.x) + fabsf(v01.y), l11 = fabsf(v11.x) + fabsf(v11.y);
-    const float lmax = fmaxf(fmaxf(l00, l10), fmaxf(l01, l11));
+    const float ym = fmaf((float)(j + 1), hy, gy0);
+    const float yt = fmaf((float)(j + 2), hy, gy0);
+    // largest vertex bound and |alpha|_1 over both cells (the culling tests
+    // use these; the triangle tests use each vertex's own)
+    const float emax = fmaxf(fmaxf(fmaxf(v00.z, v10.z), fmaxf(v01.z, v11.z)),
+                             fmaxf(v02.z, v12.z));
+    const float lmax =
+        fmaxf(fmaxf(fmaxf(fabsf(v00.x) + fabsf(v00.y), fabsf(v10.x) + fabsf(v10.y)),
+                    fmaxf(fabsf(v01.x) + fabsf(v01.y), fabsf(v11.x) + fabsf(v11.y))),
+              fmaxf(fabsf(v02.x) + fabsf(v02.y), fabsf(v12.x) + fabsf(v12.y)));
     {
       const float inf = __int_as_float(0x7f800000);
       StripBox box;
-      box.tx0 = warp_min(valid ? xl : inf);
-      box.tx1 = warp_max(valid ? xr : -inf);
-      box.ty0 = warp_min(valid ? yb : inf);
-      box.ty1 = warp_max(valid ? yt : -inf);
-      box.ax0 = warp_min(valid ? fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)) : inf);
-      box.ax1 = warp_max(valid ? fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)) : -inf);
-      box.ay0 = warp_min(valid ? fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)) : inf);
-      box.ay1 = warp_max(valid ? fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)) : -inf);
-      box.e = warp_max(valid ? emax : 0.0f);
-      box.l = warp_max(valid ? lmax : 0.0f);
-      box.any = __any_sync(0xffffffffu, valid) ? 1 : 0;
+      box.tx0 = warp_min(validA ? xl : inf);
+      box.tx1 = warp_max(validA ? xr : -inf);
+      box.ty0 = warp_min(validA ? yb : inf);
+      box.ty1 = warp_max(validA ? (validB ? yt : ym) : -inf);
+      box.ax0 = warp_min(validA ? fminf(fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)),
+                                        fminf(v02.x, v12.x))
+                                : inf);
+      box.ax1 = warp_max(validA ? fmaxf(fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)),
+                                        fmaxf(v02.x, v12.x))
+                                : -inf);
+      box.ay0 = warp_min(validA ? fminf(fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)),
+                                        fminf(v02.y, v12.y))
+                                : inf);
+      box.ay1 = warp_max(validA ? fmaxf(fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)),
+                                        fmaxf(v02.y, v12.y))
+                                : -inf);
+      box.e = warp_max(validA ? emax : 0.0f);
+      box.l = warp_max(validA ? lmax : 0.0f);
+      box.any = __any_sync(0xffffffffu, validA) ? 1 : 0;
       box.pad = 0;
       if (lane == 0) sb[wid] = box;
     }
@@ -245,65 +304,69 @@ __global__ void __launch_bounds__(kSearchThreads, 6)
       for (int q = 0; q < ns; ++q) {
         const int k = surv[wid][q];
         const SrcSmem S = ss[k];
-        const float dl = xl - S.px, dr = xr - S.px, db = yb - S.py, dt = yt - S.py;
+        const float dl = xl - S.px, dr = xr - S.px;
+        const float db = yb - S.py, dm = ym - S.py, dt = yt - S.py;
         // relative mapped vertices beta_v - P = (theta_v - P) - r alpha_v
         const float a00x = fmaf(-S.r, v00.x, dl), a00y = fmaf(-S.r, v00.y, db);
         const float a10x = fmaf(-S.r, v10.x, dr), a10y = fmaf(-S.r, v10.y, db);
-        const float a01x = fmaf(-S.r, v01.x, dl), a01y = fmaf(-S.r, v01.y, dt);
-        const float a11x = fmaf(-S.r, v11.x, dr), a11y = fmaf(-S.r, v11.y, dt);
-        const float dmax = fmaxf(fabsf(dl), fabsf(dr)) + fmaxf(fabsf(db), fabsf(dt));
-        const float mu = fmaf(S.r, emax, S.mu0 + u * (2.0f * dmax + 2.0f * S.r * lmax));
-        const float minx = fminf(fminf(a00x, a10x), fminf(a01x, a11x));
-        const float maxx = fmaxf(fmaxf(a00x, a10x), fmaxf(a01x, a11x));
-        const float miny = fminf(fminf(a00y, a10y), fminf(a01y, a11y));
-        const float maxy = fmaxf(fmaxf(a00y, a10y), fmaxf(a01y, a11y));
-        const bool cand = valid && minx <= mu && maxx >= -mu && miny <= mu && maxy >= -mu;
+        const float a01x = fmaf(-S.r, v01.x, dl), a01y = fmaf(-S.r, v01.y, dm);
+        const float a11x = fmaf(-S.r, v11.x, dr), a11y = fmaf(-S.r, v11.y, dm);
+        const float a02x = fmaf(-S.r, v02.x, dl), a02y = fmaf(-S.r, v02.y, dt);
+        const float a12x = fmaf(-S.r, v12.x, dr), a12y = fmaf(-S.r, v12.y, dt);
+        const float dxm = fmaxf(fabsf(dl), fabsf(dr));
+        const float base = S.mu0 + u * 2.0f * S.r * lmax;
+        const float muA = fmaf(S.r, emax, fmaf(u * 2.0f, dxm + fmaxf(fabsf(db), fabsf(dm)), base));
+        const float muB = fmaf(S.r, emax, fmaf(u * 2.0f, dxm + fmaxf(fabsf(dm), fabsf(dt)), base));
+        const bool candA = validA && fminf(fminf(a00x, a10x), fminf(a01x, a11x)) <= muA &&
+                           fmaxf(fmaxf(a00x, a10x), fmaxf(a01x, a11x)) >= -muA &&
+                           fminf(fminf(a00y, a10y), fminf(a01y, a11y)) <= muA &&
+                           fmaxf(fmaxf(a00y, a10y), fmaxf(a01y, a11y)) >= -muA;
+        const bool candB = validB && fminf(fminf(a01x, a11x), fminf(a02x, a12x)) <= muB &&
+                           fmaxf(fmaxf(a01x, a11x), fmaxf(a02x, a12x)) >= -muB &&
+                           fminf(fminf(a01y, a11y), fminf(a02y, a12y)) <= muB &&
+                           fmaxf(fmaxf(a01y, a11y), fmaxf(a02y, a12y)) >= -muB;
+        if (!__any_sync(0xffffffffu, candA || candB)) continue;
+        // per-vertex bounds
+        auto muv = [&](const float4& v, float d) {
+          return fmaf(S.r, v.z, S.mu0 + u * (2.0f * d + 2.0f * S.r * (fabsf(v.x) + fabsf(v.y))));
+        };
         int r0 = 0, r1 = 0;
         float w0[3], w1[3], pe0 = 0.0f, pe1 = 0.0f;
-        if (cand) {
-          // per-vertex bounds
-          auto muv = [&](float e, float l, float d) {
-            return fmaf(S.r, e, S.mu0 + u * (2.0f * d + 2.0f * S.r * l));
-          };
-          const float m00 = muv(v00.z, l00, fabsf(dl) + fabsf(db));
-          const float m10 = muv(v10.z, l10, fabsf(dr) + fabsf(db));
-          const float m01 = muv(v01.z, l01, fabsf(dl) + fabsf(dt));
-          const float m11 = muv(v11.z, l11, fabsf(dr) + fabsf(dt));
+        const float m01 = muv(v01, fabsf(dl) + fabsf(dm));
+        const float m11 = muv(v11, fabsf(dr) + fabsf(dm));
+        if (candA) {
+          const float m00 = muv(v00, fabsf(dl) + fabsf(db));
+          const float m10 = muv(v10, fabsf(dr) + fabsf(db));
           // T0 = (v00, v10, v11), T1 = (v00, v11, v01)
           r0 = classify32(a00x, a00y, a10x, a10y, a11x, a11y, m00, m10, m11, w0, &pe0);
           r1 = classify32(a00x, a00y, a11x, a11y, a01x, a01y, m00, m11, m01, w1, &pe1);
         }
-        const bool ok0 = r0 == 1 && pe0 * hmax <= (float)LT_POS_TOL;
-        const bool ok1 = r1 == 1 && pe1 * hmax <= (float)LT_POS_TOL;
-        const bool wk0 = r0 == 2 || (r0 == 1 && !ok0);
-        const bool wk1 = r1 == 2 || (r1 == 1 && !ok1);
-        if (__any_sync(0xffffffffu, ok0 || ok1 || wk0 || wk1)) {
-          const int64_t tri0 = 2 * cl, tri1 = 2 * cl + 1;
-          Hit h;
-          h.src = s0 + k;
-          h.fp64 = 0;
-          h.tri = tri0;
-          h.w[0] = w0[0]; h.w[1] = w0[1]; h.w[2] = w0[2];
-          double2 xy = hit_xy(g.x0, g.y0, g.dx, g.dy, i, j, 0, w0[1], w0[2]);
-          h.x = xy.x;
-          h.y = xy.y;
-          Hit* hb = hits + (int64_t)b * hit_cap;
-          warp_append_hit(ok0, h, hb, hit_cap, hit_count + b, status);
-          h.tri = tri1;
-          h.w[0] = w1[0]; h.w[1] = w1[1]; h.w[2] = w1[2];
-          xy = hit_xy(g.x0, g.y0, g.dx, g.dy, i, j, 1, w1[1], w1[2]);
-          h.x = xy.x;
-          h.y = xy.y;
-          warp_append_hit(ok1, h, hb, hit_cap, hit_count + b, status);
-          Work64* wb = work + (int64_t)b * work_cap;
-          warp_append_work(wk0, Work64{sample, s0 + k, tri0, r0 == 2 ? 0 : 1, 0}, wb, work_cap,
-                           work_count + b, status, counters);
-          warp_append_work(wk1, Work64{sample, s0 + k, tri1, r1 == 2 ? 0 : 1, 0}, wb, work_cap,
-                           work_count + b, status, counters);
-          n_hit += (int)ok0 + (int)ok1;
-          n_amb += (int)(r0 == 2) + (int)(r1 == 2);
-          n_ref += (int)(r0 == 1 && !ok0) + (int)(r1 == 1 && !ok1);
+        bool ok0 = r0 == 1 && pe0 * hmax <= (float)LT_POS_TOL;
+        bool ok1 = r1 == 1 && pe1 * hmax <= (float)LT_POS_TOL;
+        emit_cell(g, sample, b, s0 + k, (int64_t)j * cw + i, i, j, r0, r1, w0, w1, ok0, ok1,
+                  hits, hit_cap, work, work_cap, hit_count, work_count, status, counters);
+        n_hit += (int)ok0 + (int)ok1;
+        n_amb += (int)(r0 == 2) + (int)(r1 == 2);
+        n_ref += (int)(r0 == 1 && !ok0) + (int)(r1 == 1 && !ok1);
+        r0 = 0;
+        r1 = 0;
+        pe0 = 0.0f;
+        pe1 = 0.0f;
+        if (candB) {
+          const float m02 = muv(v02, fabsf(dl) + fabsf(dt));
+          const float m12 = muv(v12, fabsf(dr) + fabsf(dt));
+          // the cell above: T0 = (v01, v11, v12), T1 = (v01, v12, v02)
+          r0 = classify32(a01x, a01y, a11x, a11y, a12x, a12y, m01, m11, m12, w0, &pe0);
+          r1 = classify32(a01x, a01y, a12x, a12y, a02x, a02y, m01, m12, m02, w1, &pe1);
         }
+        ok0 = r0 == 1 && pe0 * hmax <= (float)LT_POS_TOL;
+        ok1 = r1 == 1 && pe1 * hmax <= (float)LT_POS_TOL;
+        emit_cell(g, sample, b, s0 + k, (int64_t)(j + 1) * cw + i, i, j + 1, r0, r1, w0, w1,
+                  ok0, ok1, hits, hit_cap, work, work_cap, hit_count, work_count, status,
+                  counters);
+        n_hit += (int)ok0 + (int)ok1;
+        n_amb += (int)(r0 == 2) + (int)(r1 == 2);
+        n_ref += (int)(r0 == 1 && !ok0) + (int)(r1 == 1 && !ok1);
       }
     }
   }
