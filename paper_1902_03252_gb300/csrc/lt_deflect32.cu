@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
                                                   unsigned long long* __restrict__ next_item) {
   __shared__ float4 sp[kChunk32 * 5];
   __shared__ long long s_item;
+  grid_dependency_wait();
   for (;;) {
     // dynamic distribution of the equal-size work items: blocks that start
     // late (another kernel still resident on their SM) simply take fewer
@@ -110,10 +111,8 @@ static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int 
   int64_t blocks = (int64_t)sm_count * per_sm;
   if (blocks > n_items) blocks = n_items;
   if (blocks < 1) return cudaSuccess;
-  k_deflect32<NT, NPT, MINB><<<(unsigned)blocks, NT, 0, st>>>(pot32, seg, n_pot, grids, item_off,
-                                                          n_samples, n_items, node_out,
-                                                          next_item);
-  return cudaGetLastError();
+  return launch_pdl(k_deflect32<NT, NPT, MINB>, dim3((unsigned)blocks), dim3(NT), st, pot32, seg,
+                    n_pot, grids, item_off, n_samples, n_items, node_out, next_item);
 }
 
 template <int V>

@@ -452,6 +452,7 @@ __global__ void k_res_insert(const Work64* __restrict__ work,
                              unsigned long long* __restrict__ keys, unsigned long long mask,
                              int32_t* __restrict__ vslot, int32_t* __restrict__ ulist,
                              unsigned int* __restrict__ n_unique) {
+  grid_dependency_wait();
   const int64_t total = (int64_t)n_samples * work_cap * 3;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total;
        f += (int64_t)gridDim.x * blockDim.x) {
@@ -491,6 +492,7 @@ __global__ void __launch_bounds__(kResNodeThreads)
                 const SampleGrid* __restrict__ grids, const unsigned long long* __restrict__ keys,
                 const int32_t* __restrict__ ulist, const unsigned int* __restrict__ n_unique,
                 double2* __restrict__ hval, long long* counters) {
+  grid_dependency_wait();
   __shared__ double2 buf[kResNodeThreads];
   __shared__ double res[2];
   const unsigned int nu = *n_unique;
@@ -519,6 +521,7 @@ __global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
                           int64_t hit_cap, unsigned long long* hit_count, long long* counters,
                           uint32_t* status, unsigned long long* __restrict__ keys,
                           unsigned int* __restrict__ n_unique) {
+  grid_dependency_wait();
   // this kernel is the table's last reader: it leaves the table empty for the
   // next call (the distinct-node list count here, every used slot below)
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_unique = 0u;
@@ -590,17 +593,18 @@ cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* gr
   const int64_t slots3 = (int64_t)n_samples * work_cap * 3;
   int64_t b1 = (slots3 + 255) / 256;
   if (b1 > (int64_t)sm_count * 16) b1 = (int64_t)sm_count * 16;
-  k_res_insert<<<(unsigned)b1, 256, 0, st>>>(work, work_count, n_samples, work_cap, grids,
-                                              rs.keys, cap - 1, rs.vslot, rs.ulist, rs.n_unique);
-  k_res_nodes<<<sm_count * 8, kResNodeThreads, 0, st>>>(pot64, n_pot, src.sample_base, grids,
-                                                         rs.keys, rs.ulist, rs.n_unique, rs.hval,
-                                                         counters);
+  cudaError_t e = launch_pdl(k_res_insert, dim3((unsigned)b1), dim3(256), st, work, work_count,
+                             n_samples, work_cap, grids, rs.keys, cap - 1, rs.vslot, rs.ulist,
+                             rs.n_unique);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(k_res_nodes, dim3(sm_count * 8), dim3(kResNodeThreads), st, pot64, n_pot,
+                 src.sample_base, grids, rs.keys, rs.ulist, rs.n_unique, rs.hval, counters);
+  if (e != cudaSuccess) return e;
   int64_t b3 = ((int64_t)n_samples * work_cap + 127) / 128;
   if (b3 > (int64_t)sm_count * 16) b3 = (int64_t)sm_count * 16;
-  k_res_tri<<<(unsigned)b3, 128, 0, st>>>(grids, src, work, work_count, n_samples, work_cap,
-                                           rs.vslot, rs.hval, hits, hit_cap, hit_count, counters,
-                                           status, rs.keys, rs.n_unique);
-  return cudaGetLastError();
+  return launch_pdl(k_res_tri, dim3((unsigned)b3), dim3(128), st, grids, src, work, work_count,
+                    n_samples, work_cap, rs.vslot, rs.hval, hits, hit_cap, hit_count, counters,
+                    status, rs.keys, rs.n_unique);
 }
 
 // -------------------------------------------------------------- barycentres
@@ -734,6 +738,7 @@ __global__ void __launch_bounds__(kMatchThreads)
                  const SampleGrid* __restrict__ grids, lt_obs obs, double* __restrict__ terms,
                  int64_t* __restrict__ match_tri, int32_t* __restrict__ match_hit,
                  double* __restrict__ match_xy) {
+  grid_dependency_wait();
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * kMatchThreads + threadIdx.x) >> 5;
   if (wid >= (int64_t)n_samples * obs.n_obs) return;  // warp-uniform
@@ -794,6 +799,7 @@ __global__ void __launch_bounds__(kMatchThreads)
 __global__ void __launch_bounds__(kChi2Threads)
     k_chi2_sum(int sample_base, int n_obs, const double* __restrict__ terms,
                double* __restrict__ chi2) {
+  grid_dependency_wait();
   __shared__ double wsum[kChi2Threads / 32];
   const int sample = sample_base + blockIdx.x;
   const double* tb = terms + (int64_t)sample * n_obs;
@@ -816,13 +822,12 @@ cudaError_t launch_chi2(const Hit* hits, const unsigned long long* hit_count, in
   if (n_samples <= 0) return cudaSuccess;
   const int64_t warps = (int64_t)n_samples * obs.n_obs;
   const int64_t blocks = (warps * 32 + kMatchThreads - 1) / kMatchThreads;
-  k_chi2_match<<<(unsigned)blocks, kMatchThreads, 0, st>>>(hits, hit_count, hit_cap, n_samples,
-                                                            sample_base, grids, obs, terms,
-                                                            match_tri, match_hit, match_xy);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(k_chi2_match, dim3((unsigned)blocks), dim3(kMatchThreads), st, hits,
+                             hit_count, hit_cap, n_samples, sample_base, grids, obs, terms,
+                             match_tri, match_hit, match_xy);
   if (e != cudaSuccess) return e;
-  k_chi2_sum<<<n_samples, kChi2Threads, 0, st>>>(sample_base, obs.n_obs, terms, chi2);
-  return cudaGetLastError();
+  return launch_pdl(k_chi2_sum, dim3(n_samples), dim3(kChi2Threads), st, sample_base, obs.n_obs,
+                    terms, chi2);
 }
 
 }  // namespace lt

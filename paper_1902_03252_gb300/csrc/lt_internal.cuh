@@ -312,6 +312,37 @@ __device__ __forceinline__ int find_sample(const int64_t* off, int n, int64_t it
   return lo;
 }
 
+// ------------------------------------------------ programmatic dependent launch
+// Kernels of the chi^2 chain are launched with programmatic stream
+// serialization: the next kernel's grid may be scheduled while the previous
+// kernel of the stream drains, which hides its launch latency.  Every such
+// kernel calls grid_dependency_wait() before it touches any memory, which
+// returns once the previous kernel has completed and its writes are visible
+// (a no-op when the kernel was launched without the attribute).  Not under
+// stream capture: a CUDA graph already launches its kernels back to back, and
+// measured slower (about 8 us per c2 evaluation) with programmatic edges.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the cudaGetLastError() value.
 // Zero up to four arrays of 64-bit counters in one launch (the per-call
