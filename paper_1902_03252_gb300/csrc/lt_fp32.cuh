@@ -80,12 +80,13 @@ __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, c
 //
 // One PIEMD on the NPT nodes of a thread (one column).  The range tests of
 // the two special functions are merged into one branch per thread and
-// potential: both polynomials of atanc_sq32 / atanhc_sq32 are evaluated on the unreduced
-// arguments for every node (finite for any argument), and the nodes outside
-// their ranges (atan: t2 > 1, atanh: t2 > 0.25; about 14 % of node-potential
-// pairs on cluster lenses) are then recomputed by those functions.  Every node
-// gets exactly the values and roundings of the per-node evaluation; the
-// merged test removes most of the branch instructions from the issue stream.
+// potential: both polynomials of atanc_sq32 / atanhc_sq32 are evaluated on
+// the unreduced arguments for every node (out of range the value may
+// overflow; it is replaced), and the nodes outside their ranges (atan:
+// t2 > 1, atanh: t2 > 0.25; about 14 % of node-potential pairs on cluster
+// lenses) are then recomputed by those functions.  Every node gets exactly
+// the values and roundings of the per-node evaluation; the merged test
+// removes most of the branch instructions from the issue stream.
 template <int NPT>
 __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X, const float* Y,
                                               float* AX, float* AY, float* ER) {
@@ -123,21 +124,19 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     // the polynomials of atanc_sq32 / atanhc_sq32 on the unreduced arguments
-    float p = 2.781707901e-03f;
-    p = fmaf(p, ux[m], -1.579383570e-02f);
-    p = fmaf(p, ux[m], 4.224103530e-02f);
-    p = fmaf(p, ux[m], -7.465778757e-02f);
-    p = fmaf(p, ux[m], 1.062265347e-01f);
-    p = fmaf(p, ux[m], -1.419891983e-01f);
-    p = fmaf(p, ux[m], 1.999201744e-01f);
-    p = fmaf(p, ux[m], -3.333304396e-01f);
-    p = fmaf(p, ux[m], 9.999999824e-01f);
-    float h = 1.832424287e-01f;
-    h = fmaf(h, uy[m], 8.136755977e-02f);
-    h = fmaf(h, uy[m], 1.469695817e-01f);
-    h = fmaf(h, uy[m], 1.997503703e-01f);
-    h = fmaf(h, uy[m], 3.333387857e-01f);
-    h = fmaf(h, uy[m], 9.999999809e-01f);
+    float p = -4.583680071e-03f;
+    p = fmaf(p, ux[m], 2.386548743e-02f);
+    p = fmaf(p, ux[m], -5.894885957e-02f);
+    p = fmaf(p, ux[m], 9.877178818e-02f);
+    p = fmaf(p, ux[m], -1.400628537e-01f);
+    p = fmaf(p, ux[m], 1.996748000e-01f);
+    p = fmaf(p, ux[m], -3.333184719e-01f);
+    p = fmaf(p, ux[m], 9.999998808e-01f);
+    float h = 1.953562647e-01f;
+    h = fmaf(h, uy[m], 1.221839786e-01f);
+    h = fmaf(h, uy[m], 2.019458860e-01f);
+    h = fmaf(h, uy[m], 3.332709372e-01f);
+    h = fmaf(h, uy[m], 1.000000358e+00f);
     px_[m] = p;
     py_[m] = h;
   }

@@ -189,15 +189,18 @@ __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, in
 }
 
 // ---------------------------------------------------- FP32 special functions
-// atan(t)/t of t2 = t*t >= 0: for t2 <= 1 a degree-8 polynomial in t2
-// (least-squares fit at Chebyshev nodes, relative error < 1e-7; the
-// coefficients come from csrc/fit_poly.py); for t2 > 1, atan(t) = pi/2 -
+// atan(t)/t of t2 = t*t >= 0: for t2 <= 1 a degree-7 polynomial in t2
+// (least-squares fit at Chebyshev nodes; relative error of its FP32 Horner
+// evaluation < 1.7e-7 = 2.8 ulp, included in the deflection's error-bound
+// coefficient errGx; the coefficients come from csrc/fit_poly.py); for t2 > 1,
+// atan(t) = pi/2 -
 // atan(1/t) gives (pi/2)/t - P(1/t2)/t2 with one MUFU rsqrt.  The range test
 // is a real branch: the 32 nodes of a warp see one potential from nearly the
 // same direction, so it is almost always uniform.
 //
-// atanh(t)/t of t2 = t*t in [0, 1): for t2 <= 1/4 a degree-5 polynomial in
-// t2 (same fit, relative error < 1.1e-7); above, atanh(t) = ln((1+t)/(1-t))/2
+// atanh(t)/t of t2 = t*t in [0, 1): for t2 <= 1/4 a degree-4 polynomial in
+// t2 (same fit; relative error < 4.6e-7 = 7.7 ulp, included in errGy); above,
+// atanh(t) = ln((1+t)/(1-t))/2
 // with MUFU rsqrt, rcp and lg2 (the ratio is >= 3 there, where lg2 has a
 // 2-ulp relative error).
 __device__ __forceinline__ float atanc_sq32(float t2) {
@@ -208,15 +211,14 @@ __device__ __forceinline__ float atanc_sq32(float t2) {
     inv = r * r;
     u = inv;
   }
-  p = 2.781707901e-03f;
-  p = fmaf(p, u, -1.579383570e-02f);
-  p = fmaf(p, u, 4.224103530e-02f);
-  p = fmaf(p, u, -7.465778757e-02f);
-  p = fmaf(p, u, 1.062265347e-01f);
-  p = fmaf(p, u, -1.419891983e-01f);
-  p = fmaf(p, u, 1.999201744e-01f);
-  p = fmaf(p, u, -3.333304396e-01f);
-  p = fmaf(p, u, 9.999999824e-01f);
+  p = -4.583680071e-03f;
+  p = fmaf(p, u, 2.386548743e-02f);
+  p = fmaf(p, u, -5.894885957e-02f);
+  p = fmaf(p, u, 9.877178818e-02f);
+  p = fmaf(p, u, -1.400628537e-01f);
+  p = fmaf(p, u, 1.996748000e-01f);
+  p = fmaf(p, u, -3.333184719e-01f);
+  p = fmaf(p, u, 9.999998808e-01f);
   if (t2 > 1.0f) p = fmaf(1.57079633f, r, -(p * inv));
   return p;
 }
@@ -227,12 +229,11 @@ __device__ __forceinline__ float atanhc_sq32(float t2) {
     const float t = t2 * r;
     return __log2f(__fdividef(1.0f + t, 1.0f - t)) * (0.5f * 0.693147181f) * r;
   }
-  float p = 1.832424287e-01f;
-  p = fmaf(p, t2, 8.136755977e-02f);
-  p = fmaf(p, t2, 1.469695817e-01f);
-  p = fmaf(p, t2, 1.997503703e-01f);
-  p = fmaf(p, t2, 3.333387857e-01f);
-  p = fmaf(p, t2, 9.999999809e-01f);
+  float p = 1.953562647e-01f;
+  p = fmaf(p, t2, 1.221839786e-01f);
+  p = fmaf(p, t2, 2.019458860e-01f);
+  p = fmaf(p, t2, 3.332709372e-01f);
+  p = fmaf(p, t2, 1.000000358e+00f);
   return p;
 }
 
