@@ -9,11 +9,11 @@ polynomial and of its float32 Horner evaluation (float32 coefficients)
 against the float64 function, and the coefficients of the degrees the kernel
 uses (highest degree first, for Horner).
 
-The kernel uses degree 7 for atanc and 4 for atanhc.  Each degree less saves
+The kernel uses degree 6 for atanc and 4 for atanhc.  Each degree less saves
 one FP32 operation per node and potential in the deflection, and the larger
-approximation error (2.8 and 7.7 ulp, against 1.5 and 1.7 ulp at degrees 8
+approximation error (13.5 and 7.7 ulp, against 1.5 and 1.7 ulp at degrees 8
 and 5) is added to the error bound's coefficients errGx and errGy, which
-are about 80 and 100 ulp: the bound grows by a few per cent.
+are about 80 and 100 ulp: the bound grows by several per cent.
 
 Usage: python fit_poly.py
 """
@@ -52,7 +52,7 @@ def atanhc(u):
     return np.where(u > 0, np.arctanh(s) / np.where(s > 0, s, 1), 1.0)
 
 
-USED = {"atanc": 7, "atanhc": 4}  # degrees in the kernel
+USED = {"atanc": 6, "atanhc": 4}  # degrees in the kernel
 
 if __name__ == "__main__":
     for name, f, a, b in (("atanc", atanc, 0.0, 1.0), ("atanhc", atanhc, 0.0, U_H)):

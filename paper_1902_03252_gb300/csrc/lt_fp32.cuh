@@ -124,14 +124,13 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     // the polynomials of atanc_sq32 / atanhc_sq32 on the unreduced arguments
-    float p = -4.583680071e-03f;
-    p = fmaf(p, ux[m], 2.386548743e-02f);
-    p = fmaf(p, ux[m], -5.894885957e-02f);
-    p = fmaf(p, ux[m], 9.877178818e-02f);
-    p = fmaf(p, ux[m], -1.400628537e-01f);
-    p = fmaf(p, ux[m], 1.996748000e-01f);
-    p = fmaf(p, ux[m], -3.333184719e-01f);
-    p = fmaf(p, ux[m], 9.999998808e-01f);
+    float p = 7.685306482e-03f;
+    p = fmaf(p, ux[m], -3.647336364e-02f);
+    p = fmaf(p, ux[m], 8.325644583e-02f);
+    p = fmaf(p, ux[m], -1.345480382e-01f);
+    p = fmaf(p, ux[m], 1.987373084e-01f);
+    p = fmaf(p, ux[m], -3.332583010e-01f);
+    p = fmaf(p, ux[m], 9.999992251e-01f);
     float h = 1.953562647e-01f;
     h = fmaf(h, uy[m], 1.221839786e-01f);
     h = fmaf(h, uy[m], 2.019458860e-01f);

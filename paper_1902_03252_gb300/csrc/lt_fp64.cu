@@ -156,10 +156,10 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[3] = make_float4((float)(sig * (sc - a)), (float)(sig * q2 * (sc + a) * (sc - a)),
                            (float)(sig * q2 * (sc - a)), (float)(Bs * p.c));
       const double iq2 = 1.0 / q2;
-      // the polynomial errors of atanc / atanhc (2.8 and 7.7 ulp) are part of
-      // errGx and errGy
+      // the polynomial errors of atanc / atanhc (13.5 and 7.7 ulp) are part
+      // of errGx and errGy
       const double gy = (14.0 + 17.0 * iq2) * (1.0 + iq2) + 16.0;
-      f.f[4] = make_float4((float)(4.0 * B / q), (float)(82.0 * Bs), (float)(gy * Bs),
+      f.f[4] = make_float4((float)(4.0 * B / q), (float)(92.0 * Bs), (float)(gy * Bs),
                            (float)(Bs * p.s));
       Q = 16.0 * B * iq2;
     }

@@ -189,9 +189,9 @@ __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, in
 }
 
 // ---------------------------------------------------- FP32 special functions
-// atan(t)/t of t2 = t*t >= 0: for t2 <= 1 a degree-7 polynomial in t2
+// atan(t)/t of t2 = t*t >= 0: for t2 <= 1 a degree-6 polynomial in t2
 // (least-squares fit at Chebyshev nodes; relative error of its FP32 Horner
-// evaluation < 1.7e-7 = 2.8 ulp, included in the deflection's error-bound
+// evaluation < 8.1e-7 = 13.5 ulp, included in the deflection's error-bound
 // coefficient errGx; the coefficients come from csrc/fit_poly.py); for t2 > 1,
 // atan(t) = pi/2 -
 // atan(1/t) gives (pi/2)/t - P(1/t2)/t2 with one MUFU rsqrt.  The range test
@@ -211,14 +211,13 @@ __device__ __forceinline__ float atanc_sq32(float t2) {
     inv = r * r;
     u = inv;
   }
-  p = -4.583680071e-03f;
-  p = fmaf(p, u, 2.386548743e-02f);
-  p = fmaf(p, u, -5.894885957e-02f);
-  p = fmaf(p, u, 9.877178818e-02f);
-  p = fmaf(p, u, -1.400628537e-01f);
-  p = fmaf(p, u, 1.996748000e-01f);
-  p = fmaf(p, u, -3.333184719e-01f);
-  p = fmaf(p, u, 9.999998808e-01f);
+  p = 7.685306482e-03f;
+  p = fmaf(p, u, -3.647336364e-02f);
+  p = fmaf(p, u, 8.325644583e-02f);
+  p = fmaf(p, u, -1.345480382e-01f);
+  p = fmaf(p, u, 1.987373084e-01f);
+  p = fmaf(p, u, -3.332583010e-01f);
+  p = fmaf(p, u, 9.999992251e-01f);
   if (t2 > 1.0f) p = fmaf(1.57079633f, r, -(p * inv));
   return p;
 }
