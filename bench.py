@@ -38,7 +38,7 @@ WORKLOAD = ("c2: 100 PIEMD, 2000^2 grid over 200\", 20 systems / 72 observed ima
             "one lens sample per chi^2 evaluation")
 SM_PER_GPU_FALLBACK = 152
 # Algorithmic work of one PIEMD node x potential evaluation (difference form):
-# 61 FP32 pipe operations and 8 MUFU operations; at 128 FP32 lanes and 16
+# 60 FP32 pipe operations and 8 MUFU operations; at 128 FP32 lanes and 16
 # MUFU lanes per SM per clock the FP32 pipe allows 2.1 and the MUFU pipe 2
 # node x potential per SM-clock: the peak is the smaller, 2.
 PIEMD_NODE_POT_PER_SM_CLK = 2.0
@@ -409,7 +409,7 @@ def run_ours(a, rank, world, local):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_deflect32", "kernel_ms": defl_ms,
                      "peak_basis": f"{sm_count} SMs x {f_max / 1e6:.0f} MHz (max SM clock) x "
-                                   "2 PIEMD node.pot per SM-clock (min of 128 FP32 / 61 "
+                                   "2 PIEMD node.pot per SM-clock (min of 128 FP32 / 60 "
                                    "ops and 16 MUFU / 8 ops)"},
         "kernel_ms_per_step": {k: prof[k]["ms"] / prof_steps for k in prof},
         "stats": stats,
