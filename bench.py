@@ -248,6 +248,31 @@ def run_reference(a, rank, world):
 
 
 # --------------------------------------------------------------------- ours
+def pick_shape(m, lt, torch, grid, obs, dev_params, out, steps=30):
+    """The deflection's launch shape, chosen by timing whole evaluations (the
+    step the benchmark times) with each shape of the library's table: the
+    kernel-only autotuner does not see the barycentre kernels that share the
+    SMs at the start of a step.  Untimed setup, before the timed region."""
+    best, best_ms = 0, float("inf")
+    for v in range(m.num_shapes()):
+        m.set_shape(v)
+        for _ in range(3):
+            m.set_params(dev_params)
+            m.chi2(grid, obs, precision=lt.MIXED, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            m.set_params(dev_params)
+            m.chi2(grid, obs, precision=lt.MIXED, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if ms < best_ms * 0.997:  # a later shape must be clearly faster
+            best, best_ms = v, ms
+    m.set_shape(best)
+    return best
+
+
 def run_ours(a, rank, world, local):
     import numpy as np
     import torch
@@ -280,10 +305,10 @@ def run_ours(a, rank, world, local):
     m = lt.Model(w.n_pot, 1)
     m.set_params(w.params)
     obs = lt.Observations.from_dict(o, device=dev)
-    shape = None if a.no_autotune else m.autotune(grid[0])
     out = torch.empty(1, dtype=torch.float64, device=dev)
     dev_params = torch.as_tensor(np.ascontiguousarray(w.params), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    shape = None if a.no_autotune else pick_shape(m, lt, torch, grid, obs, dev_params, out)
 
     # correctness of the timed configuration
     m.chi2(grid, obs, precision=lt.MIXED, out=out)

@@ -276,6 +276,10 @@ class Model:
                                            _ptr(c2), _ptr(gr), _stream(stream)), "lt_chi2_grad")
         return c2, gr
 
+    def num_shapes(self) -> int:
+        """Number of launch shapes of the FP32 deflection (lt_num_shapes)."""
+        return int(self._lib.lt_num_shapes())
+
     def set_shape(self, shape: int):
         """Pin the FP32 deflection launch shape (index into the shape table)."""
         self._check(self._lib.lt_model_set_shape(self.h, int(shape)), "lt_model_set_shape")
