@@ -450,9 +450,9 @@ def run_ours(a, rank, world, local):
     }
     if not a.no_extras:
         line["hff_deflection"] = extra_hff(lt, W, torch, dev)
-        line["batched_c3"] = extra_batched(lt, W, torch, dev)
+        line["batched_c3"] = extra_batched(lt, W, torch, dev, peak * 1e9)
         line["gradient_c4"] = extra_gradient(lt, W, torch, dev)
-        line["large_c5"] = extra_large(lt, W, torch, dev)
+        line["large_c5"] = extra_large(lt, W, torch, dev, peak * 1e9)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(w, o)
     if rank == 0:
@@ -502,7 +502,7 @@ def extra_hff(lt, W, torch, dev, steps=3):
                     "halo patches and where the distortion criteria fire)"}
 
 
-def extra_batched(lt, W, torch, dev, steps=2):
+def extra_batched(lt, W, torch, dev, peak, steps=2):
     """1024 perturbed 50-PIEMD samples on grids of 500^2..2000^2, 10 systems,
     one chi^2 per sample, whole batch per call through the CUDA-graph path."""
     w = W.c3()
@@ -527,6 +527,9 @@ def extra_batched(lt, W, torch, dev, steps=2):
     m.close()
     return {"workload": "c3: 1024 samples x 50 PIEMD, grids 500^2..2000^2, 10 systems",
             "s_per_batch": t, "chi2_evals_per_s": w.batch / t, "node_pot_per_s": npot / t,
+            # the whole batch (search, FP64 resolution, matching included)
+            # against the deflection's roofline
+            "frac_of_deflection_roofline": npot / t / peak,
             "status": int(st), "stats": stats}
 
 
@@ -561,7 +564,7 @@ def extra_gradient(lt, W, torch, dev, steps=5):
             "gradient_overhead": t_grad / t_val - 1.0, "status": int(st)}
 
 
-def extra_large(lt, W, torch, dev, steps=2):
+def extra_large(lt, W, torch, dev, peak, steps=2):
     """One sample of the large workload: 1000 PIEMD, 4000^2 grid, 100 systems,
     chi^2 and gradient (the full 64-sample batch is this times 64)."""
     w = W.c5(batch=1)
@@ -579,6 +582,7 @@ def extra_large(lt, W, torch, dev, steps=2):
     return {"workload": "c5: 1000 PIEMD, 4000^2 grid, 100 systems, one sample",
             "chi2_s": t_val, "chi2_grad_s": t_grad, "deflect_shape": shape,
             "node_pot_per_s": w.grids[0].nx * w.grids[0].ny * w.n_pot / t_val,
+            "frac_of_deflection_roofline": w.grids[0].nx * w.grids[0].ny * w.n_pot / t_val / peak,
             "status": int(st), "stats": stats}
 
 
