@@ -230,8 +230,8 @@ lt_status lt_chi2_graph(lt_model* model, const lt_grid* grids, const lt_obs* obs
 
 /* Choose the launch shape of the FP32 deflection kernel by index, in
  * [0, lt_num_shapes()): (threads per block, nodes per thread, resident blocks
- * per SM its register budget allows) of (128, 4, 7) (the default),
- * (256, 2, 5), (256, 3, 4), (128, 8, 3), (128, 8, 4), (256, 4, 3), (128, 4, 8),
+ * per SM its register budget allows) of (256, 4, 3) (the default),
+ * (256, 2, 5), (256, 3, 4), (128, 8, 3), (128, 8, 4), (128, 4, 7), (128, 4, 8),
  * (256, 2, 6).  A thread's nodes are consecutive rows of one grid column.
  * Every shape computes the same values; only speed differs.  lt_autotune
  * picks one by timing.  Errors: LT_ERR_INVALID_ARG. */

@@ -48,9 +48,11 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
     // node coordinates rounded once from FP64: error u|theta| (App. A's
     // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
     const float X = (float)(g.x0 + (double)i * g.dx);
-    float Y[NPT], AX[NPT], AY[NPT], ER[NPT];
+    float Y[NPT], AX[NPT], AY[NPT], PX[NPT], PY[NPT], ER[NPT];
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
+      PX[m] = 0.0f;
+      PY[m] = 0.0f;
       Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
       AX[m] = 0.0f;
       AY[m] = 0.0f;
@@ -76,17 +78,28 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
       // kind segments [0, n_sis) SIS, [n_sis, n_sis + n_piemd) PIEMD, rest SIE
       const int e_sis = min(max(sg.n_sis - c0, 0), cn);
       const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
-      for (int k = 0; k < e_sis; ++k) {
-        const float4* f = &sp[k * 5];
-        sis32_nodes<NPT>(f, f[4].x, X, Y, AX, AY, ER);
+      // groups of at most kSumGroup potentials of one kind segment, each
+      // summed into PX, PY and then added to the totals
+      for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
+        for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k) {
+          const float4* f = &sp[k * 5];
+          sis32_nodes<NPT>(f, f[4].x, X, Y, PX, PY, ER);
+        }
+        flush_group<NPT>(AX, AY, PX, PY, ER);
       }
-      for (int k = e_sis; k < e_pie; ++k) {
-        const float4* f = &sp[k * 5];
-        piemd32_nodes<NPT>(f, f[4].x, X, Y, AX, AY, ER);
+      for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
+        for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k) {
+          const float4* f = &sp[k * 5];
+          piemd32_nodes<NPT>(f, f[4].x, X, Y, PX, PY, ER);
+        }
+        flush_group<NPT>(AX, AY, PX, PY, ER);
       }
-      for (int k = e_pie; k < cn; ++k) {
-        const float4* f = &sp[k * 5];
-        sie32_nodes<NPT>(f, f[4].x, X, Y, AX, AY, ER);
+      for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
+        for (int k = k0; k < min(k0 + kSumGroup, cn); ++k) {
+          const float4* f = &sp[k * 5];
+          sie32_nodes<NPT>(f, f[4].x, X, Y, PX, PY, ER);
+        }
+        flush_group<NPT>(AX, AY, PX, PY, ER);
       }
     }
     const float qs = sg.q_tot;

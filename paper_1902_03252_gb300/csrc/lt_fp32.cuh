@@ -14,8 +14,35 @@ namespace lt {
 // (dx c or dy s) does not change its error bound: both are at most the
 // distance times the coefficient.
 
+// Blocked summation over the potentials (Higham, "Accuracy and Stability of
+// Numerical Algorithms", ch. 4): the potentials' terms are summed into a
+// partial sum per group of kSumGroup potentials, and each group's partial sum
+// is added to the node's total.  A term's rounding is then bounded by the
+// partial sum it joins (per potential, in the functions below) and a group's
+// by the total once per group, instead of every term by the running total:
+// with n potentials the running-sum part of the bound shrinks from about
+// n |alpha| to about (kSumGroup + n / kSumGroup) |alpha|, and so does the
+// error itself.
+constexpr int kSumGroup = 32;
+
+// Add a group's partial sums to the totals (one rounding per component,
+// bounded by the new total) and clear them.
+template <int NPT>
+__device__ __forceinline__ void flush_group(float* AX, float* AY, float* PX, float* PY,
+                                            float* ER) {
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    AX[m] += PX[m];
+    AY[m] += PY[m];
+    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    PX[m] = 0.0f;
+    PY[m] = 0.0f;
+  }
+}
+
 // One SIS: alpha += b0 (theta - c)/R (zero at the centre).  err accumulates in
-// units of the FP32 unit roundoff.
+// units of the FP32 unit roundoff.  In this and the two functions below, AX
+// and AY are a group's partial sums (flush_group).
 template <int NPT>
 __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, const float* Y,
                                             float* AX, float* AY, float* ER) {

@@ -244,8 +244,8 @@ struct DeflectShape {
 };
 constexpr int kNumShapes = 8;
 __host__ __device__ constexpr DeflectShape deflect_shape(int v) {
-  const DeflectShape tab[kNumShapes] = {{128, 4, 7}, {256, 2, 5}, {256, 3, 4}, {128, 8, 3},
-                                        {128, 8, 4}, {256, 4, 3}, {128, 4, 8}, {256, 2, 6}};
+  const DeflectShape tab[kNumShapes] = {{256, 4, 3}, {256, 2, 5}, {256, 3, 4}, {128, 8, 3},
+                                        {128, 8, 4}, {128, 4, 7}, {128, 4, 8}, {256, 2, 6}};
   return tab[v < 0 || v >= kNumShapes ? 0 : v];
 }
 

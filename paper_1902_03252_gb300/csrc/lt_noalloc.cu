@@ -57,9 +57,9 @@ lt_status device_setup(int dev, unsigned char** base, int* sms) {
   return LT_OK;
 }
 
-// the default launch shape of the batched kernel: 128 threads, 4 rows each,
-// registers for 7 resident blocks per SM
-constexpr int kNT = 128, kNPT = 4, kMinBlocks = 7;
+// the default launch shape of the batched kernel: 256 threads, 4 rows each,
+// registers for 3 resident blocks per SM
+constexpr int kNT = 256, kNPT = 4, kMinBlocks = 3;
 
 // Same arithmetic as the batched deflection kernel (same per-potential
 // functions, kind segments and order), for one sample, writing alpha and the
@@ -83,9 +83,11 @@ __global__ void __launch_bounds__(kNT, kMinBlocks)
     // node coordinates rounded once from FP64: error u|theta| (App. A's
     // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
     const float X = (float)(g.x0 + (double)i * g.dx);
-    float Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
+    float Y[kNPT], AX[kNPT], AY[kNPT], PX[kNPT], PY[kNPT], ER[kNPT];
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {
+      PX[m] = 0.0f;
+      PY[m] = 0.0f;
       Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
       AX[m] = 0.0f;
       AY[m] = 0.0f;
@@ -108,12 +110,22 @@ __global__ void __launch_bounds__(kNT, kMinBlocks)
       __syncthreads();
       const int e_sis = min(max(sg.n_sis - c0, 0), cn);
       const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
-      for (int k = 0; k < e_sis; ++k)
-        sis32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
-      for (int k = e_sis; k < e_pie; ++k)
-        piemd32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
-      for (int k = e_pie; k < cn; ++k)
-        sie32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, AX, AY, ER);
+      // the batched kernel's groups of kSumGroup potentials per kind segment
+      for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
+        for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k)
+          sis32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+        flush_group<kNPT>(AX, AY, PX, PY, ER);
+      }
+      for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
+        for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k)
+          piemd32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+        flush_group<kNPT>(AX, AY, PX, PY, ER);
+      }
+      for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
+        for (int k = k0; k < min(k0 + kSumGroup, cn); ++k)
+          sie32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+        flush_group<kNPT>(AX, AY, PX, PY, ER);
+      }
     }
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {

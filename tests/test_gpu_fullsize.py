@@ -157,12 +157,12 @@ def test_c5_full_size_local_checks(oracle):
 
 
 def test_c5_work_overflow_is_reported():
-    """A c5 sample has ~16k ambiguous (triangle, source) pairs: with the
-    default per-sample capacity of 4096 the FP64 work list overflows, which
-    sync reports as LT_ERR_OVERFLOW with the dropped count, never silently."""
+    """A c5 sample has a few thousand ambiguous (triangle, source) pairs: with
+    a per-sample capacity of 256 the FP64 work list overflows, which sync
+    reports as LT_ERR_OVERFLOW with the dropped count, never silently."""
     w = W.c5(batch=1)
     o = load_obs("c5")
-    m = lt.Model(w.n_pot, 1)
+    m = lt.Model(w.n_pot, 1, hit_capacity=256)
     m.set_params(w.params)
     m.chi2([w.grids[0].as_tuple()], lt.Observations.from_dict(o), precision=lt.MIXED)
     st, stats = m.sync()
