@@ -8,9 +8,16 @@ Workload (one step = one chi^2 evaluation of one lens-parameter sample):
   tests/golden/obs_c2.json), mixed precision; the FP64 form is timed beside it.
 
 Metric: chi^2 evaluations/s (whole job) and node x potential deflections/s.
-Each rank evaluates its own samples (independent MCMC proposals): weak
-scaling, no collective on the data path (a barrier and a max-reduction of the
-timings only).
+Each rank evaluates its own proposals (independent MCMC chains, Sect. 2.2.1):
+weak scaling, no collective on the data path.  The batched workload (1024
+samples on uneven grids) is sharded over the ranks by work, and its per-sample
+chi^2 values are gathered to every rank in sample order afterwards.
+
+Besides the headline line's keys, the line carries the other workloads: the
+single-SIS latency case, the 1024-sample batch, the gradient case, the large
+case as its full 64-sample batch with chi^2 and gradients, the paper's own
+deflection benchmark, the FP64 form against the FP64 pipe, and the oracle's
+CPU time for every workload (full or on a stated subset).
 
 --impl reference runs the FP64 CPU oracle on the host cores instead (rank 0),
 on a bounded band of the same workload per step.
@@ -40,8 +47,16 @@ SM_PER_GPU_FALLBACK = 152
 # Algorithmic work of one PIEMD node x potential evaluation (difference form):
 # 60 FP32 pipe operations and 8 MUFU operations; at 128 FP32 lanes and 16
 # MUFU lanes per SM per clock the FP32 pipe allows 2.1 and the MUFU pipe 2
-# node x potential per SM-clock: the peak is the smaller, 2.
+# node x potential per SM-clock: the roofline is the smaller, 2.  (The kernel
+# issues fewer instructions than 60 + 8 per node x potential, because most
+# range reductions are skipped; what limits it in practice is instruction
+# issue, about one warp instruction per clock per SM sub-partition.)
 PIEMD_NODE_POT_PER_SM_CLK = 2.0
+# The plain FP64 form: GB300 runs FP64 at 1/64 of the FP32 rate, 2 FP64
+# lanes per SM per clock.  FP64 pipe operations per PIEMD node x potential,
+# counted from the formula (52 add/mul/sub, 6 sqrt, 8 div, 2 atan, 2 atanh)
+# with each library function's FP64 pipe operations as executed (ncu).
+FP64_LANES_PER_SM_CLK = 2.0
 
 
 def parse():
@@ -185,18 +200,64 @@ def traffic_for(kernel: str, files):
     return None
 
 
-def cpu_baseline_oracle(w, o, seconds_hint=15.0):
-    """One full chi^2 evaluation of the workload by the FP64 oracle."""
+def load_golden(cfg):
+    with open(os.path.join(ROOT, "tests", "golden", f"obs_{cfg}.json")) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------- CPU baseline
+def _oracle_eval_s(oracle, params, grid, obs, threads, rows=None):
+    """Seconds of one oracle chi^2 evaluation (deflection on all cores,
+    barycentres, triangle search over cell rows on all cores, matching), on
+    the whole grid or on its first ``rows`` cell rows."""
+    g = grid if rows is None else (grid[0], grid[1], grid[2], grid[3], grid[4], rows + 1)
+    t0 = time.perf_counter()
+    oracle.chi2(params, g, obs, n_threads=threads, capacity=1 << 18)
+    return time.perf_counter() - t0
+
+
+def cpu_baselines(W):
+    """The oracle as it stands, on the host's cores: every workload's chi^2
+    evaluations/s, whole evaluations where they take seconds (c1, c2, c4) and
+    stated subsets scaled to whole evaluations otherwise (c3: two samples of
+    the batch, each in full; c5: a band of cell rows of one sample)."""
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    res = oracle.chi2(w.params[0], w.grids[0].as_tuple(), o, n_threads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "one full chi^2 evaluation of the workload (deflection on all cores, "
-                      "triangle search single-threaded)",
-            "seconds": dt, "chi2": res["chi2"]}
+    out = {}
+
+    def whole(name, w, o):
+        dt = _oracle_eval_s(oracle, w.params[0], w.grids[0].as_tuple(), o, threads)
+        out[name] = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                     "seconds_per_chi2": dt,
+                     "node_pot_per_s": w.grids[0].nodes * w.n_pot / dt,
+                     "sample": "one full chi^2 evaluation"}
+
+    whole("c1", W.c1(), load_golden("c1"))
+    whole("c2", W.c2(), load_golden("c2"))
+    whole("c4", W.c4(), load_golden("c4"))
+    w3, o3 = W.c3(), load_golden("c3")
+    picks = [0, 1]
+    t3 = sum(_oracle_eval_s(oracle, w3.params[b], w3.grids[b].as_tuple(), o3, threads)
+             for b in picks)
+    nodes3 = sum(w3.grids[b].nodes for b in picks)
+    per_node = t3 / nodes3
+    batch_s = per_node * sum(g.nodes for g in w3.grids)
+    out["c3"] = {"value": w3.batch / batch_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+                 "seconds_per_batch": batch_s,
+                 "sample": f"samples {picks} of the 1024 in full ({t3:.1f} s), scaled to the "
+                           "batch by its node count"}
+    w5, o5 = W.c5(batch=1), load_golden("c5")
+    g5 = w5.grids[0].as_tuple()
+    rows = 60
+    t5 = _oracle_eval_s(oracle, w5.params[0], g5, o5, threads, rows=rows)
+    full5 = t5 * (g5[5] - 1) / rows
+    out["c5"] = {"value": 1.0 / full5, "unit": UNIT, "cores": threads, "kind": "oracle",
+                 "seconds_per_chi2": full5,
+                 "sample": f"{rows} of {g5[5] - 1} cell rows of one sample ({t5:.1f} s: "
+                           "deflection, barycentres and search of that band), scaled to "
+                           "the whole grid"}
+    return out
 
 
 # --------------------------------------------------------------- reference
@@ -204,8 +265,6 @@ def run_reference(a, rank, world):
     """The FP64 oracle on the host cores, each step a band of grid rows."""
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
     from paper_1902_03252_gb300 import workloads as W
     oracle.build()
@@ -238,13 +297,22 @@ def run_reference(a, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic",
+        "config": config_of(a, precision="fp64 (oracle)", shape=None),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{rows} of {g.ny - 1} cell rows per step (deflection and "
                                    "triangle search of that band), scaled to whole evaluations"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def config_of(a, precision, shape):
+    """The workload description shared by both arms' lines."""
+    return {"workload": WORKLOAD, "precision": precision,
+            "l2": "flushed between timed steps (256 MB write outside the step events)",
+            "step": "parameter preparation from device-resident parameters + chi^2",
+            "clock_warmup_s": a.clock_warmup, "deflect_shape": shape}
 
 
 # --------------------------------------------------------------------- ours
@@ -298,15 +366,16 @@ def run_ours(a, rank, world, local):
         return float(t.item())
 
     w = W.c2()
+    params = W.c2_proposal(rank)  # every rank evaluates its own proposal
     o = load_obs()
     grid = [w.grids[0].as_tuple()]
     nodes = w.grids[0].nodes
     node_pot = nodes * w.n_pot
     m = lt.Model(w.n_pot, 1)
-    m.set_params(w.params)
+    m.set_params(params)
     obs = lt.Observations.from_dict(o, device=dev)
     out = torch.empty(1, dtype=torch.float64, device=dev)
-    dev_params = torch.as_tensor(np.ascontiguousarray(w.params), dtype=torch.float64, device=dev)
+    dev_params = torch.as_tensor(np.ascontiguousarray(params), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     shape = None if a.no_autotune else pick_shape(m, lt, torch, grid, obs, dev_params, out)
 
@@ -366,8 +435,20 @@ def run_ours(a, rank, world, local):
     ms_mixed = max_over_ranks(ms_mixed)
     value = world * 1000.0 / ms_mixed
 
+    # stage breakdown: stages 0-3 run one after another on the stream, so
+    # with k_prep and the counter reset they make up the step; the
+    # barycentres run on a side stream under the deflection
     prof_steps = max(1, min(a.steps, 50))
-    _, _, prof, _ = timed(lt.MIXED, prof_steps, 1, lt.PROFILE_KINDS)
+    ms_prof, _, prof, _ = timed(lt.MIXED, prof_steps, 1, lt.PROFILE_KINDS)
+    stage_ms = {k: prof[k]["ms"] / prof_steps for k in prof}
+    seq = sum(stage_ms[k] for k in ("deflect", "search", "resolve", "chi2"))
+    breakdown = {"deflect": stage_ms["deflect"], "search": stage_ms["search"],
+                 "fp64_resolve": stage_ms["resolve"], "match_chi2": stage_ms["chi2"],
+                 "prep_reset_and_gaps": ms_prof - seq, "step": ms_prof,
+                 "barycentres_overlapped": stage_ms["bary"],
+                 "note": "the first five add up to the step (the profiled steps carry one "
+                         "event pair per stage); the barycentres run on a side stream "
+                         "during the deflection"}
     ms64, _, prof64, _ = timed(lt.FP64, max(1, min(a.steps, a.fp64_steps)), 1, ("deflect",))
     ms64 = max_over_ranks(ms64)
     value64 = world * 1000.0 / ms64
@@ -379,7 +460,7 @@ def run_ours(a, rank, world, local):
     # is bracketed by CUDA events from the upload to the download, the host
     # waits for the result, and L2 is flushed between steps (outside the
     # brackets), as for the device-timed steps.
-    host_params = torch.from_numpy(np.ascontiguousarray(w.params)).pin_memory()
+    host_params = torch.from_numpy(np.ascontiguousarray(params)).pin_memory()
     host_out = torch.empty(1, dtype=torch.float64).pin_memory()
     for _ in range(a.warmup):
         m.set_params(host_params.numpy())
@@ -413,6 +494,17 @@ def run_ours(a, rank, world, local):
     traffic = traffic_for("k_deflect32", DEFLECT32_SOURCES)
     d64 = prof64["deflect"]
     defl64_ms = d64["ms"] / max(1, d64["launches"])
+    fp64_ops = fp64_ops_per_node_pot()
+    fp64_roof = None
+    if fp64_ops:
+        ach64 = node_pot / (defl64_ms * 1e-3) * fp64_ops  # FP64 pipe operations / s
+        pk64 = sm_count * f_max * FP64_LANES_PER_SM_CLK
+        fp64_roof = {"bound": "fp64", "kernel": "k_deflect64", "kernel_ms": defl64_ms,
+                     "fp64_ops_per_node_pot": fp64_ops,
+                     "achieved": ach64 / 1e9, "peak": pk64 / 1e9, "unit": "G FP64 ops/s",
+                     "frac": ach64 / pk64,
+                     "peak_basis": f"{sm_count} SMs x {f_max / 1e6:.0f} MHz x 2 FP64 lanes "
+                                   "per SM-clock (1/64 of the FP32 rate)"}
     launches_per_step = sum(prof[k]["launches"] for k in prof) / prof_steps
 
     line = {
@@ -420,23 +512,23 @@ def run_ours(a, rank, world, local):
         "warmup": a.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 predicate fallback, f64 chi2)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "mixed",
-                   "l2": "flushed between timed steps (256 MB write outside the step events)",
-                   "step": "parameter preparation from device-resident parameters + chi^2",
-                   "clock_warmup_s": a.clock_warmup,
-                   "deflect_shape": shape},
+        "config": config_of(a, precision="mixed", shape=shape),
         "node_pot_per_s": value * node_pot,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64,
                  "node_pot_per_s": value64 * node_pot,
-                 "deflect_kernel_ms": defl64_ms},
+                 "deflect_kernel_ms": defl64_ms, "roofline": fp64_roof},
         "mixed_over_fp64": value / value64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gnode_pot/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per "
+                                       "launch from the committed ncu capture in profiles/ "
+                                       "(used only while the kernel's source hash matches; "
+                                       "null otherwise)",
                      "kernel": "k_deflect32", "kernel_ms": defl_ms,
                      "peak_basis": f"{sm_count} SMs x {f_max / 1e6:.0f} MHz (max SM clock) x "
                                    "2 PIEMD node.pot per SM-clock (min of 128 FP32 / 60 "
                                    "ops and 16 MUFU / 8 ops)"},
-        "kernel_ms_per_step": {k: prof[k]["ms"] / prof_steps for k in prof},
+        "kernel_ms_per_step": breakdown,
         "stats": stats,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,
                 "h2d_bytes_per_step": int(host_params.numel() * 8),
@@ -448,89 +540,43 @@ def run_ours(a, rank, world, local):
         "wall_s_timed_region": wall,
         "deflect32_source_sha256": source_sha(DEFLECT32_SOURCES),
     }
+    m.close()
+    del flush
     if not a.no_extras:
-        line["hff_deflection"] = extra_hff(lt, W, torch, dev)
-        line["batched_c3"] = extra_batched(lt, W, torch, dev, peak * 1e9)
-        line["gradient_c4"] = extra_gradient(lt, W, torch, dev)
-        line["large_c5"] = extra_large(lt, W, torch, dev, peak * 1e9)
+        # the batch is sharded over the ranks; the other workloads run on rank 0
+        line["batched_c3"] = extra_batched(lt, W, torch, dev, peak * 1e9, rank, world,
+                                           max_over_ranks, barrier)
+        if rank == 0:
+            line["latency_c1"] = extra_latency(lt, W, torch, dev)
+            line["gradient_c4"] = extra_gradient(lt, W, torch, dev)
+            line["large_c5"] = extra_large(lt, W, torch, dev, peak * 1e9)
+            line["hff_deflection"] = extra_hff(lt, W, torch, dev)
+        barrier()
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_oracle(w, o)
+        cb = cpu_baselines(W)
+        line["cpu_baseline"] = dict(cb["c2"], sample="one full chi^2 evaluation of the "
+                                    "workload (deflection and triangle search on all cores)")
+        line["cpu_baseline_all"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
-    m.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def extra_hff(lt, W, torch, dev, steps=3):
-    """The paper's benchmark (Sect. 4): deflection of 6730^2 pixels at 0.03"
-    by 2 cluster + 700 galaxy SIE, FP32 (with its running bound) and FP64."""
-    w = W.hff()
-    grid = w.grids[0].as_tuple()
-    n = w.grids[0].nx
-    m = lt.Model(w.n_pot, 1)
-    m.set_params(w.params)
-    shape = m.autotune(grid)
-    a32 = torch.empty((n, n, 2), dtype=torch.float32, device=dev)
-
-    def time_it(fn, k):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(k):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / k / 1e3
-
-    t32 = time_it(lambda: m.deflect_grid(grid, precision=lt.MIXED), steps)
-    del a32
-    t_paper = time_it(lambda: m.deflect_grid(grid, precision=lt.PAPER), steps)
-    st, stats = m.sync()
-    t64 = time_it(lambda: m.deflect_grid(grid, precision=lt.FP64), 1)
-    m.close()
-    npot = w.grids[0].nodes * w.n_pot
-    return {"workload": "6730^2 pixels at 0.03\", 2 cluster + 700 galaxy SIE (Sect. 4)",
-            "node_pot": npot, "fp32_s": t32, "fp64_s": t64, "paper_mixed_s": t_paper,
-            "paper_mixed_fp64_nodes": stats["fp64_nodes"], "deflect_shape": shape,
-            "fp32_node_pot_per_s": npot / t32, "fp64_node_pot_per_s": npot / t64,
-            "paper_s": {"V100": {"dp": 0.46, "mixed": 0.39}, "P100": {"dp": 0.71, "mixed": 0.58},
-                        "GTX1080Ti": {"dp": 6.8, "mixed": 1.58}, "Xeon12c": {"dp": 8.1, "mixed": 7.40}},
-            "note": "deflection grid only, as timed in the paper; fp32 is the grid with its "
-                    "per-node error bound; paper_mixed is the paper's rule (FP32, then FP64 in "
-                    "halo patches and where the distortion criteria fire)"}
-
-
-def extra_batched(lt, W, torch, dev, peak, steps=2):
-    """1024 perturbed 50-PIEMD samples on grids of 500^2..2000^2, 10 systems,
-    one chi^2 per sample, whole batch per call through the CUDA-graph path."""
-    w = W.c3()
-    with open(os.path.join(ROOT, "tests", "golden", "obs_c3.json")) as f:
-        o = json.load(f)
-    grids = [g.as_tuple() for g in w.grids]
-    m = lt.Model(w.n_pot, w.batch)
-    m.set_params(w.params)
-    obs = lt.Observations.from_dict(o, device=dev)
-    out = torch.empty(w.batch, dtype=torch.float64, device=dev)
-    m.chi2(grids, obs, precision=lt.MIXED, out=out, graph=True)
-    st, stats = m.sync()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        m.chi2(grids, obs, precision=lt.MIXED, out=out, graph=True)
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / steps / 1e3
-    npot = w.node_pot()
-    m.close()
-    return {"workload": "c3: 1024 samples x 50 PIEMD, grids 500^2..2000^2, 10 systems",
-            "s_per_batch": t, "chi2_evals_per_s": w.batch / t, "node_pot_per_s": npot / t,
-            # the whole batch (search, FP64 resolution, matching included)
-            # against the deflection's roofline
-            "frac_of_deflection_roofline": npot / t / peak,
-            "status": int(st), "stats": stats}
+def fp64_ops_per_node_pot():
+    """FP64 pipe operations of one PIEMD node x potential in the FP64
+    deflection, as recorded in the committed ncu capture of k_deflect64
+    (profiles/k_deflect64_*.md), or None."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if name.startswith("k_deflect64") and name.endswith(".md"):
+            with open(os.path.join(pdir, name)) as f:
+                mm = re.search(r"fp64_ops_per_node_pot:\s*([0-9.eE+]+)", f.read())
+            if mm:
+                return float(mm.group(1))
+    return None
 
 
 def _time(fn, torch, steps):
@@ -545,12 +591,110 @@ def _time(fn, torch, steps):
     return e0.elapsed_time(e1) / steps / 1e3
 
 
+def extra_latency(lt, W, torch, dev, steps=200):
+    """The single-SIS case (256^2 nodes): time per chi^2, device-timed and as
+    the host sees it (parameters in, chi^2 back, waiting for each result)."""
+    w = W.c1()
+    o = load_golden("c1")
+    grid = [w.grids[0].as_tuple()]
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    obs = lt.Observations.from_dict(o, device=dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    host_out = torch.empty(1, dtype=torch.float64).pin_memory()
+    t_dev = _time(lambda: m.chi2(grid, obs, precision=lt.MIXED, out=out), torch, steps)
+    t_graph = _time(lambda: m.chi2(grid, obs, precision=lt.MIXED, out=out, graph=True), torch,
+                    steps)
+    for _ in range(5):
+        m.set_params(w.params)
+        m.chi2(grid, obs, precision=lt.MIXED, out=out, graph=True)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        m.set_params(w.params)
+        m.chi2(grid, obs, precision=lt.MIXED, out=out, graph=True)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    t_host = (time.perf_counter() - t0) / steps
+    st, _ = m.sync()
+    m.close()
+    return {"workload": "c1: one SIS, 256^2 grid over 100\", one system", "status": int(st),
+            "ms_per_chi2_device": t_dev * 1e3, "ms_per_chi2_graph": t_graph * 1e3,
+            "ms_per_chi2_host_roundtrip": t_host * 1e3,
+            "note": "device: back-to-back eager calls; graph: lt_chi2_graph replays; host "
+                    "roundtrip: host parameters in, chi^2 out, the host waiting for every "
+                    "result (wall clock)"}
+
+
+def extra_hff(lt, W, torch, dev, steps=3):
+    """The paper's benchmark (Sect. 4): deflection of 6730^2 pixels at 0.03"
+    by 2 cluster + 700 galaxy SIE, FP32 (with its running bound) and FP64."""
+    w = W.hff()
+    grid = w.grids[0].as_tuple()
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    shape = m.autotune(grid)
+    t32 = _time(lambda: m.deflect_grid(grid, precision=lt.MIXED), torch, steps)
+    t_paper = _time(lambda: m.deflect_grid(grid, precision=lt.PAPER), torch, steps)
+    st, stats = m.sync()
+    t64 = _time(lambda: m.deflect_grid(grid, precision=lt.FP64), torch, 1)
+    m.close()
+    npot = w.grids[0].nodes * w.n_pot
+    return {"workload": "6730^2 pixels at 0.03\", 2 cluster + 700 galaxy SIE (Sect. 4)",
+            "node_pot": npot, "fp32_s": t32, "fp64_s": t64, "paper_mixed_s": t_paper,
+            "paper_mixed_fp64_nodes": stats["fp64_nodes"], "deflect_shape": shape,
+            "fp32_node_pot_per_s": npot / t32, "fp64_node_pot_per_s": npot / t64,
+            "paper_s": {"V100": {"dp": 0.46, "mixed": 0.39}, "P100": {"dp": 0.71, "mixed": 0.58},
+                        "GTX1080Ti": {"dp": 6.8, "mixed": 1.58}, "Xeon12c": {"dp": 8.1, "mixed": 7.40}},
+            "note": "deflection grid only, as timed in the paper; fp32 is the grid with its "
+                    "per-node error bound; paper_mixed is the paper's rule (FP32, then FP64 in "
+                    "halo patches and where the distortion criteria fire)"}
+
+
+def extra_batched(lt, W, torch, dev, peak, rank, world, max_over_ranks, barrier, steps=3):
+    """1024 perturbed 50-PIEMD samples on grids of 500^2..2000^2, 10 systems,
+    one chi^2 per sample, each rank's shard per call through the CUDA-graph
+    path; the deflection's launch shape from the library's autotuner on the
+    shard's median grid; the per-sample chi^2 gathered in sample order."""
+    from paper_1902_03252_gb300 import sharding
+    w = W.c3()
+    o = load_golden("c3")
+    work = [g.nodes * w.n_pot for g in w.grids]
+    mine = sharding.shard_for(work, rank, world)
+    grids = [w.grids[b].as_tuple() for b in mine]
+    m = lt.Model(w.n_pot, len(mine))
+    m.set_params(w.params[mine])
+    med = sorted(grids, key=lambda g: g[4] * g[5])[len(grids) // 2]
+    shape = m.autotune(med)
+    obs = lt.Observations.from_dict(o, device=dev)
+    out = torch.empty(len(mine), dtype=torch.float64, device=dev)
+    m.chi2(grids, obs, precision=lt.MIXED, out=out, graph=True)
+    st, stats = m.sync()
+    torch.cuda.synchronize()
+    barrier()
+    t = _time(lambda: m.chi2(grids, obs, precision=lt.MIXED, out=out, graph=True), torch, steps)
+    t = max_over_ranks(t)
+    chi2 = sharding.gather_in_order(out.cpu().tolist(), mine, w.batch)
+    npot = w.node_pot()
+    m.close()
+    return {"workload": "c3: 1024 samples x 50 PIEMD, grids 500^2..2000^2, 10 systems",
+            "ranks": world, "samples_per_rank": [len(s) for s in
+                                                  sharding.balanced_shards(work, world)],
+            "deflect_shape": shape, "s_per_batch": t, "chi2_evals_per_s": w.batch / t,
+            "node_pot_per_s": npot / t,
+            # the whole batch (search, FP64 resolution, matching included)
+            # against the deflection's roofline (per GPU)
+            "frac_of_deflection_roofline": npot / t / (peak * world),
+            "chi2_gathered": len(chi2), "chi2_sum": float(sum(chi2)),
+            "status": int(st), "stats": stats}
+
+
 def extra_gradient(lt, W, torch, dev, steps=5):
     """chi^2 with d chi^2/d(x, y, e, phi, r_core, sigma_v) of 100 PIEMD on the
     1000^2 grid with 20 systems, against chi^2 alone, mixed precision."""
     w = W.c4()
-    with open(os.path.join(ROOT, "tests", "golden", "obs_c4.json")) as f:
-        o = json.load(f)
+    o = load_golden("c4")
     grid = [w.grids[0].as_tuple()]
     m = lt.Model(w.n_pot, 1)
     m.set_params(w.params)
@@ -565,24 +709,27 @@ def extra_gradient(lt, W, torch, dev, steps=5):
 
 
 def extra_large(lt, W, torch, dev, peak, steps=2):
-    """One sample of the large workload: 1000 PIEMD, 4000^2 grid, 100 systems,
-    chi^2 and gradient (the full 64-sample batch is this times 64)."""
-    w = W.c5(batch=1)
-    with open(os.path.join(ROOT, "tests", "golden", "obs_c5.json")) as f:
-        o = json.load(f)
-    grid = [w.grids[0].as_tuple()]
-    m = lt.Model(w.n_pot, 1, hit_capacity=1 << 17)
+    """The large workload as stated: a batch of 64 samples of 1000 PIEMD on
+    4000^2 grids with 100 systems, chi^2 and gradients in one call (chunked
+    by the model's workspace budget), mixed precision."""
+    w = W.c5()
+    o = load_golden("c5")
+    grids = [g.as_tuple() for g in w.grids]
+    m = lt.Model(w.n_pot, w.batch, hit_capacity=1 << 16)
     m.set_params(w.params)
-    shape = m.autotune(grid[0])
+    shape = m.autotune(grids[0])
     obs = lt.Observations.from_dict(o, device=dev)
-    t_val = _time(lambda: m.chi2(grid, obs, precision=lt.MIXED), torch, steps)
-    t_grad = _time(lambda: m.chi2_grad(grid, obs, precision=lt.MIXED), torch, steps)
+    t_val = _time(lambda: m.chi2(grids, obs, precision=lt.MIXED), torch, steps)
+    t_grad = _time(lambda: m.chi2_grad(grids, obs, precision=lt.MIXED), torch, steps)
     st, stats = m.sync()
     m.close()
-    return {"workload": "c5: 1000 PIEMD, 4000^2 grid, 100 systems, one sample",
-            "chi2_s": t_val, "chi2_grad_s": t_grad, "deflect_shape": shape,
-            "node_pot_per_s": w.grids[0].nx * w.grids[0].ny * w.n_pot / t_val,
-            "frac_of_deflection_roofline": w.grids[0].nx * w.grids[0].ny * w.n_pot / t_val / peak,
+    npot = w.node_pot()
+    return {"workload": "c5: 64 samples x 1000 PIEMD, 4000^2 grids, 100 systems, chi^2 and "
+                        "gradients per call", "batch": w.batch,
+            "chi2_s_per_batch": t_val, "chi2_grad_s_per_batch": t_grad,
+            "chi2_evals_per_s": w.batch / t_val, "chi2_grad_evals_per_s": w.batch / t_grad,
+            "deflect_shape": shape, "node_pot_per_s": npot / t_val,
+            "frac_of_deflection_roofline": npot / t_val / peak,
             "status": int(st), "stats": stats}
 
 

@@ -247,15 +247,19 @@ int32_t lt_num_shapes(void);
 lt_status lt_autotune(lt_model* model, const lt_grid* grid, uintptr_t stream, int32_t* choice);
 
 /* Per-kernel timing of later compute calls (off by default).  When enabled,
- * every launch of the deflection, search, FP64-resolution and chi^2 kernels
- * issued by lt_chi2 / lt_find_images is bracketed by CUDA events recorded
- * on the caller's stream (not inside lt_chi2_graph).  lt_profile_read waits
- * for the recorded events and returns the totals since the last reset. */
+ * every launch of the deflection, search, FP64-resolution, chi^2 and
+ * barycentre kernels issued by lt_chi2 / lt_find_images is bracketed by CUDA
+ * events recorded on the stream it runs on (not inside lt_chi2_graph).
+ * Stages 0-3 run one after another on the caller's stream, so their times
+ * add up; stage 4 runs on the model's side stream, overlapping stage 0.
+ * lt_profile_read waits for the recorded events and returns the totals since
+ * the last reset. */
 typedef struct {
-  int64_t launches[4]; /* kernel launches of [0] the deflection, [1] the
+  int64_t launches[5]; /* kernel launches of [0] the deflection, [1] the
                           search, [2] the FP64 resolution (3 kernels per
-                          chunk), [3] barycentres (2) + chi^2 (1) */
-  double ms[4];        /* summed event durations of those stages (one event
+                          chunk), [3] matching + chi^2 (2 per chunk), [4] the
+                          barycentres (2, on the side stream) */
+  double ms[5];        /* summed event durations of those stages (one event
                           pair per stage and chunk) */
   double node_pot[2];  /* node x potential evaluations by the deflection
                           launches: [0] FP32, [1] FP64 */
@@ -264,8 +268,8 @@ lt_status lt_profile_enable(lt_model* model, int on);
 lt_status lt_profile_read(lt_model* model, lt_profile* out, int reset);
 
 /* Like lt_profile_enable, for a subset of the stages: bit k of mask brackets
- * stage k (0 deflection, 1 search, 2 FP64 resolution, 3 barycentres + chi^2);
- * 0 turns timing off.  Each bracketed stage records two events per chunk on
+ * stage k (0 deflection, 1 search, 2 FP64 resolution, 3 matching + chi^2,
+ * 4 barycentres); 0 turns timing off.  Each bracketed stage records two events per chunk on
  * the stream, so timing only the stage of interest keeps the overhead of a
  * measured evaluation small.  Errors: LT_ERR_INVALID_ARG. */
 lt_status lt_profile_stages(lt_model* model, uint32_t mask);
@@ -286,10 +290,16 @@ lt_status lt_profile_stages(lt_model* model, uint32_t mask);
  * Its scratch is a fixed file-scope device array of about 0.8 MiB that every
  * GPU loading the library holds until exit; the call itself allocates
  * nothing.  The first call on a device resolves that array's address
- * (cudaGetSymbolAddress, with the device current): make that first call
- * before any stream capture.  All calls on a device share the array, so
- * calls that overlap on the GPU (different streams, or threads) race; order
- * them on one stream. */
+ * (cudaGetSymbolAddress, with the device current).  Under CUDA's lazy module
+ * loading (the default) that first call is also when the library's device
+ * code and this array are loaded onto the device, which does take device
+ * memory: make one warm-up call before the process reserves its device
+ * memory, outside any allocator hook, and before any stream capture; later
+ * calls allocate nothing.  The address is kept per device index for the life
+ * of the process: do not call this entry point after cudaDeviceReset, or with
+ * a context other than the device's primary context current.  All calls on a
+ * device share the array, so calls that overlap on the GPU (different
+ * streams, or threads) race; order them on one stream. */
 lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot, const lt_grid* grid,
                                   float* alpha_out, float* err_out, int32_t* status_out,
                                   uintptr_t stream);

@@ -281,3 +281,70 @@ def dls_ds(z_l, z_s, omega_m=0.3, omega_lambda=0.7):
     m1, m2 = dm(z_l), dm(z_s)
     okc = max(ok, 0.0)
     return (m2 * np.sqrt(1 + okc * m1 * m1) - m1 * np.sqrt(1 + okc * m2 * m2)) / m2
+
+
+# ------------------------------------------------- the paper's mixed rule
+PAPER_PIXEL = 0.03          # arcsec: the pixel size the criteria are stated for
+PAPER_T12 = 0.0092          # arcsec: |dx - delta_1,2| below this => DP (magnification > 3.26)
+PAPER_T34 = 0.0104          # arcsec: |delta_3,4| above this => DP
+PAPER_CLUSTER_B0 = 1.0      # arcsec: b0 at or above this is a cluster-scale halo
+PAPER_HALF_CLUSTER = 200    # 400 x 400 pixel DP patch around cluster-scale halos
+PAPER_HALF_GALAXY = 10      # 20 x 20 pixel DP patch around galaxy-scale halos
+
+
+def paper_flags(alpha, grid, params, dtype=np.float32):
+    """Nodes the paper's mixed rule recomputes in double precision (Sect. 3.3
+    and App. A.3): [ny][nx] bool.
+
+    alpha: [ny][nx][2] single-precision gradient grid (the rule is evaluated on
+    the SP values, as in the paper); grid: (x0, y0, dx, dy, nx, ny); params:
+    [8][n_pot] of one sample.
+
+    1. Distortion criteria.  With the left neighbour (theta_1 - dx) and the
+       lower neighbour (theta_2 - dy) of a node,
+         delta_1 = a_1(node) - a_1(left),  delta_2 = a_2(node) - a_2(lower),
+         delta_3 = a_1(node) - a_1(lower), delta_4 = a_2(node) - a_2(left);
+       the node is flagged if |dx - delta_1| or |dy - delta_2| is below the
+       0.0092" threshold (axis magnification above 3.26, with D_ls/D_s = 1,
+       the paper's worst case), or |delta_3| or |delta_4| exceeds 0.0104".
+       Both thresholds are stated for 0.03" pixels; a grid uses them scaled
+       by its spacing along the difference (dx for delta_1 and delta_4, dy
+       for delta_2 and delta_3) over 0.03", and the pixel length of the
+       delta_1,2 criterion is that spacing.  Nodes of the first row and column
+       have no neighbour and no criterion.  The differences and comparisons
+       are taken in `dtype` (single precision: the grid's own).
+    2. Halo patches: 400 x 400 pixels around every cluster-scale halo
+       (b0 >= 1") and 20 x 20 around every galaxy-scale one, centred on the
+       node nearest the halo centre (ties away from zero; rows and columns
+       [c - half, c + half)).  A potential of zero mass is no halo and has
+       no patch.
+    """
+    x0, y0, dx, dy, nx, ny = grid
+    a = np.asarray(alpha).astype(dtype)
+    assert a.shape == (ny, nx, 2), a.shape
+    hx, hy = dtype(dx), dtype(dy)
+    t12x = dtype(PAPER_T12) * hx / dtype(PAPER_PIXEL)
+    t12y = dtype(PAPER_T12) * hy / dtype(PAPER_PIXEL)
+    t34x = dtype(PAPER_T34) * hx / dtype(PAPER_PIXEL)
+    t34y = dtype(PAPER_T34) * hy / dtype(PAPER_PIXEL)
+    a1, a2 = a[..., 0], a[..., 1]
+    d1 = a1[1:, 1:] - a1[1:, :-1]
+    d2 = a2[1:, 1:] - a2[:-1, 1:]
+    d3 = a1[1:, 1:] - a1[:-1, 1:]
+    d4 = a2[1:, 1:] - a2[1:, :-1]
+    flags = np.zeros((ny, nx), bool)
+    flags[1:, 1:] = ((np.abs(hx - d1) < t12x) | (np.abs(hy - d2) < t12y) |
+                     (np.abs(d3) > t34y) | (np.abs(d4) > t34x))
+    p = _params(params)
+    b0 = 4.0 * np.pi * (p[7] / 299792.458) ** 2 * 206264.80625
+    for k in range(p.shape[1]):
+        if not b0[k] > 0.0:
+            continue
+        half = PAPER_HALF_CLUSTER if b0[k] >= PAPER_CLUSTER_B0 else PAPER_HALF_GALAXY
+        fi, fj = (p[1, k] - x0) / dx, (p[2, k] - y0) / dy
+        ic = int(np.copysign(np.floor(abs(fi) + 0.5), fi))
+        jc = int(np.copysign(np.floor(abs(fj) + 0.5), fj))
+        r0, r1 = max(jc - half, 0), max(min(jc + half, ny), 0)
+        c0, c1 = max(ic - half, 0), max(min(ic + half, nx), 0)
+        flags[r0:r1, c0:c1] = True
+    return flags

@@ -367,13 +367,21 @@ int64_t lto_find_images(const double* params, int n_pot, double x0, double y0, d
                         int64_t* n_und) {
   Grid g{x0, y0, dx, dy, nx, ny};
   size_t nn = (size_t)nx * ny;
+  const int nt = n_threads > 0 ? n_threads : 1;
   std::vector<double> alpha(2 * nn), asum(nn);
-  deflect_grid(params, n_pot, g, n_threads, alpha.data(), asum.data());
+  deflect_grid(params, n_pot, g, nt, alpha.data(), asum.data());
   std::vector<Vtx> beta(nn);
   std::vector<double> dv(nn);
+  // hits and undecidable pairs of each cell row, concatenated in row order
+  // afterwards: the lists are in (source, triangle) order whatever the
+  // number of threads
+  const int rows = ny > 1 ? ny - 1 : 0;
+  std::vector<std::vector<lto_hit>> row_hits(rows);
+  std::vector<std::vector<lto_pair>> row_und(rows);
   int64_t count = 0, ucount = 0;
   for (int s = 0; s < n_src; ++s) {
     double rs = r[s];
+#pragma omp parallel for schedule(static) num_threads(nt)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         size_t n = (size_t)j * nx + i;
@@ -384,22 +392,22 @@ int64_t lto_find_images(const double* params, int n_pot, double x0, double y0, d
       }
     Vtx P{src_xy[2 * s], src_xy[2 * s + 1]};
     double dp = d_src ? d_src[s] : 0.0;
-    int64_t ntri = 2 * (int64_t)(nx - 1) * (ny - 1);
-    for (int64_t tri = 0; tri < ntri; ++tri) {
-      int64_t v[3];
-      tri_nodes(g, tri, v);
-      Vtx A = beta[v[0]], B = beta[v[1]], C = beta[v[2]];
-      double w[3];
-      bool in = point_in_tri(A, B, C, P, w);
-      double d = std::max(std::max(dv[v[0]], dv[v[1]]), std::max(dv[v[2]], dp));
-      bool und_pair = undecidable(A, B, C, P, d);
-      if (und_pair) {
-        if (ucount < und_cap) und[ucount] = lto_pair{s, in ? 1 : 0, tri};
-        ++ucount;
-      }
-      if (in) {
-        if (count < capacity) {
-          lto_hit& h = hits[count];
+    int64_t tri_per_row = 2 * (int64_t)(nx - 1);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int jr = 0; jr < rows; ++jr) {
+      row_hits[jr].clear();
+      row_und[jr].clear();
+      for (int64_t tri = jr * tri_per_row; tri < (jr + 1) * tri_per_row; ++tri) {
+        int64_t v[3];
+        tri_nodes(g, tri, v);
+        Vtx A = beta[v[0]], B = beta[v[1]], C = beta[v[2]];
+        double w[3];
+        bool in = point_in_tri(A, B, C, P, w);
+        double d = std::max(std::max(dv[v[0]], dv[v[1]]), std::max(dv[v[2]], dp));
+        bool und_pair = undecidable(A, B, C, P, d);
+        if (und_pair) row_und[jr].push_back(lto_pair{s, in ? 1 : 0, tri});
+        if (in) {
+          lto_hit h;
           h.src = s;
           h.undecidable = und_pair ? 1 : 0;
           h.tri = tri;
@@ -410,7 +418,17 @@ int64_t lto_find_images(const double* params, int n_pot, double x0, double y0, d
           int64_t ic = v[2] % nx, jc = v[2] / nx;
           h.x = w[0] * g.X((int)ia) + w[1] * g.X((int)ib) + w[2] * g.X((int)ic);
           h.y = w[0] * g.Y((int)ja) + w[1] * g.Y((int)jb) + w[2] * g.Y((int)jc);
+          row_hits[jr].push_back(h);
         }
+      }
+    }
+    for (int jr = 0; jr < rows; ++jr) {
+      for (const lto_pair& u : row_und[jr]) {
+        if (ucount < und_cap) und[ucount] = u;
+        ++ucount;
+      }
+      for (const lto_hit& h : row_hits[jr]) {
+        if (count < capacity) hits[count] = h;
         ++count;
       }
     }

@@ -64,45 +64,3 @@ if __name__ == "__main__":
             if deg == USED[name]:
                 print("  coefficients:", ", ".join(f"{v:.9e}f" for v in c))
 
-
-def fit_rational(f, a, b, p_deg, q_deg, n=4000, iters=30):
-    """Relative least-squares rational fit P(u)/Q(u), Q(0) = 1, by iterated
-    linearisation (Loeb / Sanathanan-Koerner), float64."""
-    k = np.arange(n)
-    x = (a + b) / 2 + (b - a) / 2 * np.cos(np.pi * (k + 0.5) / n)
-    y = f(x)
-    w = np.ones_like(x)
-    for _ in range(iters):
-        # P(x) - y (Q(x) - 1) = y, unknowns: p_0..p_P, q_1..q_Q ; weight 1/(y Q_prev)
-        A = np.hstack([np.vander(x, p_deg + 1), -y[:, None] * np.vander(x, q_deg + 1)[:, :-1]])
-        A = A * (w / y)[:, None]
-        c, *_ = np.linalg.lstsq(A, w, rcond=None)
-        pc, qc = c[:p_deg + 1], np.append(c[p_deg + 1:], 1.0)
-        w = 1.0 / np.abs(np.polyval(qc, x))
-    return pc, qc
-
-
-def check_rational(f, pc, qc, a, b):
-    x = np.linspace(a, b, 200001)
-    y = f(x)
-    r64 = np.polyval(pc, x) / np.polyval(qc, x)
-    xf = x.astype(np.float32)
-    def horner32(c):
-        acc = np.float32(c[0])
-        for ci in c[1:]:
-            acc = (acc * xf + np.float32(ci)).astype(np.float32)
-        return acc
-    r32 = (horner32(pc) / horner32(qc)).astype(np.float32)
-    return np.max(np.abs(r64 / y - 1)), np.max(np.abs(r32.astype(np.float64) / y - 1))
-
-
-if __name__ == "__main__":
-    UR = 0.8
-    for pd, qd in ((2, 2), (3, 2), (3, 3), (4, 3), (4, 4)):
-        pc, qc = fit_rational(atanhc, 0.0, UR, pd, qd)
-        e64, e32 = check_rational(atanhc, pc, qc, 0.0, UR)
-        print(f"atanhc rational ({pd},{qd}) on [0,{UR}]: rel err f64 {e64:.2e} f32 {e32:.2e}")
-        if e64 < 5e-8:
-            print("  P:", ", ".join(f"{v:.9e}f" for v in pc))
-            print("  Q:", ", ".join(f"{v:.9e}f" for v in qc))
-            break

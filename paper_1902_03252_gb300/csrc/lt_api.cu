@@ -474,7 +474,7 @@ lt_status enqueue_chi2(lt_model* m, const lt_obs& obs, int precision, double* ch
   LT_CUDA(cudaEventRecord(m->ev_fork, st));
   LT_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
   {
-    ProfScope ps(m, m->side, 3, 0.0, 0, 2);  // k_bary_obs, k_bary_sys
+    ProfScope ps(m, m->side, 4, 0.0, 0, 2);  // k_bary_obs, k_bary_sys
     LT_CUDA(launch_barycentres(m->d_pot64, m->n_pot, m->batch, obs, m->d_beta_obs, m->d_bary,
                                m->side));
   }
@@ -888,13 +888,13 @@ lt_status lt_model_sync(lt_model* m, uintptr_t stream, lt_stats* stats) {
 
 lt_status lt_profile_enable(lt_model* m, int on) {
   if (!m) return LT_ERR_INVALID_ARG;
-  m->prof_mask = on ? 0xfu : 0u;
+  m->prof_mask = on ? 0x1fu : 0u;
   return LT_OK;
 }
 
 lt_status lt_profile_stages(lt_model* m, uint32_t mask) {
   if (!m) return LT_ERR_INVALID_ARG;
-  LT_CHECK_ARG(mask <= 0xfu, "stage mask has bits beyond the four stages");
+  LT_CHECK_ARG(mask <= 0x1fu, "stage mask has bits beyond the five stages");
   m->prof_mask = mask;
   return LT_OK;
 }

@@ -57,11 +57,13 @@ class Stats(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4),
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5),
                 ("node_pot", C.c_double * 2)]
 
 
-PROFILE_KINDS = ("deflect", "search", "resolve", "bary_chi2")
+# stages 0-3 run in sequence on the caller's stream; "bary" runs on the
+# model's side stream, overlapping the deflection
+PROFILE_KINDS = ("deflect", "search", "resolve", "chi2", "bary")
 
 IMAGE_DTYPE = np.dtype([("sample", "<i4"), ("src", "<i4"), ("tri", "<i8"), ("x", "<f8"),
                         ("y", "<f8"), ("w", "<f8", (3,)), ("fp64", "<i4"), ("reserved", "<i4")])

@@ -1,8 +1,10 @@
 """Host-side logic of the multi-GPU path.
 
 Samples of a batch are independent problems (separate lens-parameter
-proposals), so ranks share no data: each rank evaluates the samples of its
-shard with its own model, and only timings are reduced (a barrier and a
+proposals, Sect. 2.2.1), so ranks share no data: each rank evaluates the
+samples of its shard with its own model.  No collective touches the data
+path; afterwards the per-sample chi^2 values are gathered in sample order
+(the result a sampler needs) and the timings are reduced (a barrier and a
 maximum).  Shards balance the work of uneven grids (node x potential
 evaluations dominate) with a deterministic greedy longest-first assignment.
 """
@@ -44,3 +46,33 @@ def reduce_max(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def gather_in_order(values: Sequence[float], shard: Sequence[int], n_total: int) -> List[float]:
+    """Per-sample results of every rank's shard, placed in sample order.
+
+    ``values[k]`` is this rank's result for sample ``shard[k]``.  Every rank
+    receives the full list of ``n_total`` values (an all-gather of the
+    (index, value) pairs; with one process it is a plain reorder).  Each
+    sample must belong to exactly one shard.
+    """
+    import torch.distributed as dist
+    if len(values) != len(shard):
+        raise ValueError("one value per sample of the shard")
+    pairs = [(int(i), float(v)) for i, v in zip(shard, values)]
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        parts = [None] * dist.get_world_size()
+        dist.all_gather_object(parts, pairs)
+    else:
+        parts = [pairs]
+    out: List[float] = [float("nan")] * n_total
+    seen = [False] * n_total
+    for part in parts:
+        for i, v in part:
+            if not 0 <= i < n_total or seen[i]:
+                raise ValueError(f"sample {i} out of range or in two shards")
+            seen[i] = True
+            out[i] = v
+    if not all(seen):
+        raise ValueError("some samples belong to no shard")
+    return out

@@ -222,4 +222,17 @@ def hff(n: int = 6730, pixel: float = 0.03) -> Workload:
     return Workload("hff", p[None], [g], 0, 6000)
 
 
+
+
+def c2_proposal(rank: int) -> np.ndarray:
+    """The c2 lens as proposal number ``rank`` of independent sampler chains,
+    shape [1][8][n_pot]: rank 0 is the c2 draw itself, every other rank a
+    perturbation of it (each continuous parameter times 1 + 0.01 N(0,1),
+    seeded by the rank), so that every rank evaluates its own proposal."""
+    base = c2().params[0]
+    if rank == 0:
+        return base[None].copy()
+    return perturb(base, _rng(2, 100 + rank), 1)
+
+
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c5": c5, "hff": hff}

@@ -1,5 +1,6 @@
-"""D_ls/D_s from redshifts (lt_dls_ds, host code of the library) against the
-oracle's adaptive quadrature and against closed forms."""
+"""D_ls/D_s from redshifts: the oracle's adaptive quadrature pinned to the
+closed forms of three Friedmann models, and the library's host code
+(lt_dls_ds) against both."""
 import math
 
 import pytest
@@ -15,6 +16,30 @@ def lib():
     except RuntimeError as e:
         pytest.skip(f"cannot build the library here: {e}")
     return lt
+
+
+def closed_forms(zl, zs):
+    """(omega_m, omega_lambda, D_ls/D_s) of the Einstein-de Sitter, de Sitter
+    and Milne models, whose comoving distances have closed forms."""
+    dc = lambda z: 2 * (1 - 1 / math.sqrt(1 + z))       # EdS: D_C = 2 (1 - 1/sqrt(1+z))
+    eds = (dc(zs) - dc(zl)) / dc(zs)
+    ds = (zs - zl) / zs                                  # de Sitter: D_C = z
+    dm = lambda z: ((1 + z) - 1 / (1 + z)) / 2           # Milne: D_M = sinh(ln(1+z))
+    m1, m2 = dm(zl), dm(zs)
+    milne = (m2 * math.sqrt(1 + m1 * m1) - m1 * math.sqrt(1 + m2 * m2)) / m2
+    return [(1.0, 0.0, eds), (0.0, 1.0, ds), (0.0, 0.0, milne)]
+
+
+@pytest.mark.parametrize("zl,zs", [(0.3, 2.0), (0.05, 0.5), (1.0, 6.0)])
+def test_oracle_closed_forms(oracle, zl, zs):
+    for om, ol, exp in closed_forms(zl, zs):
+        assert oracle.dls_ds(zl, zs, om, ol) == pytest.approx(exp, rel=1e-12), (om, ol)
+
+
+def test_oracle_limits(oracle):
+    # a source just behind the lens sees no lensing; a lens at z = 0 gives 1
+    assert oracle.dls_ds(0.5, 0.5 + 1e-9) == pytest.approx(0.0, abs=1e-8)
+    assert oracle.dls_ds(1e-12, 2.0) == pytest.approx(1.0, rel=1e-9)
 
 
 def test_closed_forms(lib):

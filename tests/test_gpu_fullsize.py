@@ -1,14 +1,18 @@
 """Parity at the workloads' full sizes, in the configuration the benchmark runs.
 
 * c2 (100 PIEMD, 2000^2, 20 systems): the oracle's whole chi^2 evaluation
-  (matches, positions, chi^2) against both precisions.
+  (matches, positions, chi^2) against both precisions, and the complete image
+  set of every system -- each (system, triangle) pair the oracle finds, and
+  no other -- with every image position.
 * c3 (1024 perturbed samples, grids 500^2..2000^2, one call): the full oracle
-  evaluation of three samples drawn from the batch.
-* c5 (1000 PIEMD, 4000^2, 100 systems; two samples): outputs the oracle checks
-  one by one -- barycentres, the FP64 containment and barycentric position of
-  every matched triangle, sampled node deflections within their bound -- and
-  sampled gradient components against central differences of the oracle's
-  frozen-assignment chi^2.
+  evaluation and the complete image sets of eight samples drawn from the
+  batch.
+* c5 (1000 PIEMD, 4000^2, 100 systems): one sample against the oracle's full
+  evaluation on all host cores (image sets, matches, chi^2; slow), and on two
+  samples the outputs the oracle checks one by one -- barycentres, the FP64
+  containment and barycentric position of every matched triangle, sampled
+  node deflections within their bound -- and sampled gradient components
+  against central differences of the oracle's frozen-assignment chi^2.
 """
 import json
 import math
@@ -60,6 +64,35 @@ def run(w, o, grids, prec, grad=False, capacity=0):
     return out
 
 
+def gpu_image_sets(w, grids, bary, r, prec, capacity):
+    """Images of the given barycentres (the oracle's: the same source
+    positions on both sides) found by lt_find_images on the whole batch, as one
+    {(src, tri): (x, y)} dict per sample."""
+    m = lt.Model(w.n_pot, w.batch, hit_capacity=capacity)
+    m.set_params(w.params)
+    sx = torch.as_tensor(np.ascontiguousarray(bary, dtype=np.float64), device="cuda")
+    rr = torch.as_tensor(np.ascontiguousarray(r, dtype=np.float64), device="cuda")
+    out, n = m.find_images(grids, sx, rr, precision=prec, capacity=capacity)
+    st, stats = m.sync()
+    assert st == lt.LT_OK, (st, stats)
+    imgs = lt.images_to_numpy(out, n)
+    m.close()
+    return [{(int(h["src"]), int(h["tri"])): (float(h["x"]), float(h["y"])) for h in im}
+            for im in imgs], stats
+
+
+def assert_same_images(got, ref_hits, tol, what):
+    """The GPU image set equals the oracle's exactly; positions within tol."""
+    ref = {(h["src"], h["tri"]): (h["x"], h["y"]) for h in ref_hits}
+    assert not any(h["undecidable"] for h in ref_hits), what
+    missing, extra = set(ref) - set(got), set(got) - set(ref)
+    assert not missing and not extra, (what, sorted(missing)[:5], sorted(extra)[:5])
+    d = max((max(abs(got[k][0] - ref[k][0]), abs(got[k][1] - ref[k][1])) for k in ref),
+            default=0.0)
+    assert d <= tol, (what, d)
+    return len(ref)
+
+
 @pytest.mark.parametrize("prec,tol", [(lt.MIXED, 1e-4), (lt.FP64, 1e-9)])
 def test_c2_full_chi2(oracle, prec, tol):
     w = W.c2()
@@ -73,6 +106,11 @@ def test_c2_full_chi2(oracle, prec, tol):
     assert np.abs(r["mxy"][0][ok] - ref["match_xy"][ok]).max() <= tol
     np.testing.assert_allclose(r["bary"][0], ref["bary"], rtol=0, atol=1e-10)
     assert abs(r["chi2"][0] - ref["chi2"]) <= chi2_tol(o, ref["match_xy"], tol) + 1e-12 * ref["chi2"]
+    # the complete image set of every system, found from the oracle's barycentres
+    sets, stats = gpu_image_sets(w, [grid], ref["bary"][None], np.asarray(o["dls_ds"])[None],
+                                 prec, 4096)
+    n = assert_same_images(sets[0], ref["hits"], tol, "c2")
+    print(f"c2 precision {prec}: {n} images identical to the oracle's; stats {stats}")
 
 
 def test_c3_full_batch_sampled(oracle):
@@ -81,7 +119,14 @@ def test_c3_full_batch_sampled(oracle):
     grids = [g.as_tuple() for g in w.grids]
     r = run(w, o, grids, lt.MIXED)
     rng = np.random.default_rng(33)
-    for b in rng.choice(w.batch, 3, replace=False):
+    picks = rng.choice(w.batch, 8, replace=False)
+    # barycentres of every sample (cheap), so that the image search runs on the
+    # whole batch in its batched configuration
+    bary = np.stack([oracle.barycentres(w.params[b], o)[0] for b in range(w.batch)])
+    rr = np.broadcast_to(np.asarray(o["dls_ds"]), (w.batch, len(o["dls_ds"])))
+    sets, stats = gpu_image_sets(w, grids, bary, rr, lt.MIXED, 4096)
+    total = 0
+    for b in picks:
         ref = oracle.chi2(w.params[b], grids[b], o, n_threads=THREADS)
         assert ref["n_undecidable"] == 0
         assert np.array_equal(r["mt"][b], ref["match_tri"]), b
@@ -89,6 +134,33 @@ def test_c3_full_batch_sampled(oracle):
         assert np.abs(r["mxy"][b][ok] - ref["match_xy"][ok]).max() <= 1e-4
         assert abs(r["chi2"][b] - ref["chi2"]) <= chi2_tol(o, ref["match_xy"], 1e-4) + \
             1e-12 * ref["chi2"]
+        np.testing.assert_array_equal(bary[b], ref["bary"])
+        total += assert_same_images(sets[b], ref["hits"], 1e-4, f"c3 sample {b}")
+    print(f"c3: {total} images of 8 samples identical to the oracle's; batch stats {stats}")
+
+
+@pytest.mark.slow
+def test_c5_full_sample_against_full_oracle(oracle):
+    """One c5 sample (1000 PIEMD, 4000^2 nodes, 100 systems) against the
+    oracle's complete evaluation on all host cores: every image of every
+    system, the matches, the positions and chi^2, in mixed precision."""
+    w = W.c5(batch=1)
+    o = load_obs("c5")
+    grid = w.grids[0].as_tuple()
+    cap = 1 << 17
+    r = run(w, o, [grid], lt.MIXED, capacity=cap)
+    ref = oracle.chi2(w.params[0], grid, o, n_threads=THREADS, capacity=1 << 18)
+    assert ref["n_undecidable"] == 0
+    assert np.array_equal(r["mt"][0], ref["match_tri"])
+    ok = ref["match_tri"] >= 0
+    assert np.abs(r["mxy"][0][ok] - ref["match_xy"][ok]).max() <= 1e-4
+    np.testing.assert_allclose(r["bary"][0], ref["bary"], rtol=0, atol=1e-10)
+    assert abs(r["chi2"][0] - ref["chi2"]) <= chi2_tol(o, ref["match_xy"], 1e-4) + \
+        1e-12 * ref["chi2"]
+    sets, stats = gpu_image_sets(w, [grid], ref["bary"][None], np.asarray(o["dls_ds"])[None],
+                                 lt.MIXED, cap)
+    n = assert_same_images(sets[0], ref["hits"], 1e-4, "c5")
+    print(f"c5: {n} images identical to the oracle's; stats {stats}")
 
 
 def tri_nodes(grid, tri):

@@ -101,22 +101,10 @@ def test_paper_mixed_rule(oracle):
     ap, flag = ap.cpu().numpy(), flag.cpu().numpy() > 0.5
     st, stats = m.sync()
     assert st == lt.LT_OK
-    # expected flags: halo patches (closed form) and the criteria on the FP32 grid
-    exp = np.zeros((n, n), bool)
-    b0 = 4 * math.pi * (p[7] / C_KMS) ** 2 * ARCSEC
-    for k in range(p.shape[1]):
-        half = 200 if b0[k] >= 1.0 else 10
-        ic, jc = int(round((p[1, k] - grid[0]) / h)), int(round((p[2, k] - grid[1]) / h))
-        exp[max(jc - half, 0):max(min(jc + half, n), 0), max(ic - half, 0):max(min(ic + half, n), 0)] = True
-    a1, a2 = a32[..., 0], a32[..., 1]
-    hf = np.float32(h)
-    t12, t34 = np.float32(0.0092) * hf / np.float32(0.03), np.float32(0.0104) * hf / np.float32(0.03)
-    d1 = a1[1:, 1:] - a1[1:, :-1]
-    d2 = a2[1:, 1:] - a2[:-1, 1:]
-    d3 = a1[1:, 1:] - a1[:-1, 1:]
-    d4 = a2[1:, 1:] - a2[1:, :-1]
-    crit = (np.abs(hf - d1) < t12) | (np.abs(hf - d2) < t12) | (np.abs(d3) > t34) | (np.abs(d4) > t34)
-    exp[1:, 1:] |= crit
+    # expected flags: the oracle's statement of the rule (halo patches and the
+    # criteria of Sect. 3.3), evaluated on the FP32 grid in single precision
+    # as the paper does
+    exp = oracle.paper_flags(a32, grid, p)
     assert np.array_equal(flag, exp), (flag.sum(), exp.sum())
     assert stats["fp64_nodes"] == int(exp.sum())
     # unflagged nodes are the FP32 values, flagged ones the FP64 evaluation
@@ -136,6 +124,25 @@ def test_paper_mixed_rule(oracle):
     rx, ry, _ = oracle.alpha_points(p, x, y)
     d = np.maximum(np.abs(ap[uj[sel], ui[sel], 0] - rx), np.abs(ap[uj[sel], ui[sel], 1] - ry))
     assert d.max() <= g["total_sp_bound"], d.max()
+    # independently of the FP32 grid: the rule on the oracle's own FP64 grid
+    # (rounded to FP32) flags the same nodes, except where a criterion lies
+    # within twice the paper's SP error bound of its threshold (outside the
+    # patches, where that bound holds at both nodes of a difference)
+    ref, _ = oracle.deflect_grid(p, grid, n_threads=os.cpu_count() or 4)
+    f64 = oracle.paper_flags(ref.astype(np.float32), grid, p)
+    diff = f64 != flag
+    r1, r2 = ref[..., 0], ref[..., 1]
+    margin = np.full((n, n), np.inf)
+    e = 2 * g["total_sp_bound"]
+    t12, t34 = 0.0092 * h / 0.03, 0.0104 * h / 0.03
+    mg = np.minimum.reduce([np.abs(np.abs(h - (r1[1:, 1:] - r1[1:, :-1])) - t12),
+                           np.abs(np.abs(h - (r2[1:, 1:] - r2[:-1, 1:])) - t12),
+                           np.abs(np.abs(r1[1:, 1:] - r1[:-1, 1:]) - t34),
+                           np.abs(np.abs(r2[1:, 1:] - r2[1:, :-1]) - t34)])
+    margin[1:, 1:] = mg
+    print(f"paper rule: {int(flag.sum())} flagged, {int(diff.sum())} differ from the rule "
+          "on the FP64 grid")
+    assert np.all(margin[diff] <= e), margin[diff].max()
 
 
 def test_hff_full_size_sampled(oracle):

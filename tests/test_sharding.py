@@ -41,9 +41,13 @@ def _worker(rank, world, port, q):
     out = [None] * world
     dist.all_gather_object(out, mine)
     t = sharding.reduce_max(float(rank + 1) * 1.5)
+    # per-sample placeholder results (10 x sample index + 0.5), computed only
+    # by the rank that owns the sample, gathered back in sample order
+    vals = [10.0 * i + 0.5 for i in mine]
+    full = sharding.gather_in_order(vals, mine, len(work))
     dist.barrier()
     dist.destroy_process_group()
-    q.put((rank, out, t))
+    q.put((rank, out, t, full))
 
 
 def test_two_rank_gloo_sharding_and_max():
@@ -58,8 +62,18 @@ def test_two_rank_gloo_sharding_and_max():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, out, t in res:
+    for rank, out, t, full in res:
         assert t == 3.0  # max over ranks of (rank + 1) * 1.5
         flat = sorted(i for s in out for i in s)
         assert flat == list(range(16))
         assert not (set(out[0]) & set(out[1]))
+        assert out[0] and out[1]  # both ranks own samples
+        assert full == [10.0 * i + 0.5 for i in range(16)]  # every rank, sample order
+
+
+def test_gather_in_order_single_process_and_errors():
+    with pytest.raises(ValueError):
+        sharding.gather_in_order([1.0], [0], 2)            # sample 1 in no shard
+    with pytest.raises(ValueError):
+        sharding.gather_in_order([1.0, 2.0], [0, 0], 1)    # sample 0 twice
+    assert sharding.gather_in_order([2.0, 1.0], [1, 0], 2) == [1.0, 2.0]

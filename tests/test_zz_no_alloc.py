@@ -3,12 +3,17 @@
 It exists for callers that cannot allocate device memory (allocator hooks,
 memory-pool callbacks, plugins of applications that own every device
 allocation): its scratch is a fixed device array inside the library.  These
-tests call it through the C ABI and check it against the model-based
-lt_deflect_grid (mixed precision) -- the deflection within the FP32 running
-error bound that the other deflection tests use, the bound itself to 1e-6
-relative -- on two calls in a row with different models, so that the second
-call runs on the scratch contents the first one left behind.  This file is
-collected last; it passes alone in a fresh process and after the others.
+tests call it through the C ABI on two calls in a row with different models,
+so that the second call runs on the scratch contents the first one left
+behind, and check each call
+* against the FP64 oracle directly: every node within the FP32 running error
+  bound the call itself returns, the bar of the other deflection tests;
+* against the model-based lt_deflect_grid in mixed precision: the same
+  arithmetic in the same order, so deflection and bound are bit-identical;
+* for allocations: the device's free memory is the same before and after a
+  call.
+This file is collected last; it passes alone in a fresh process and after the
+others.
 """
 import ctypes as C
 
@@ -69,16 +74,39 @@ def models():
     return [big, small]
 
 
-def test_two_calls_in_a_row_match_model_path(noalloc):
+def test_two_calls_in_a_row_match_oracle_and_model_path(noalloc, oracle):
     grid = (-100.0, -100.0, 200.0 / 499, 200.0 / 499, 500, 500)
     for params in models():
         ref_a, ref_e = reference(params, grid)
         rc, a, e, st = call(noalloc, params, grid)
         assert rc == lt.LT_OK and st == lt.LT_OK
         a, e = a.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
-        assert np.all(np.isfinite(a)) and np.all(np.isfinite(e))
-        assert np.all(np.abs(a - ref_a).max(axis=-1) <= ref_e)
-        np.testing.assert_allclose(e, ref_e, rtol=1e-6)
+        assert np.all(np.isfinite(a)) and np.all(np.isfinite(e)) and np.all(e > 0)
+        # the oracle: |alpha_FP32 - alpha_FP64| within the call's own bound
+        exact, _ = oracle.deflect_grid(params, grid, n_threads=4)
+        assert np.all(np.abs(a - exact).max(axis=-1) <= e)
+        # the model path: bit-identical deflection and bound
+        np.testing.assert_array_equal(a, ref_a)
+        np.testing.assert_array_equal(e, ref_e)
+
+
+def test_call_allocates_no_device_memory(noalloc):
+    grid = (-100.0, -100.0, 200.0 / 299, 200.0 / 299, 300, 300)
+    params = models()[1]
+    call(noalloc, params, grid)  # first call: module and scratch set-up
+    p = torch.as_tensor(np.ascontiguousarray(params), dtype=torch.float64, device="cuda")
+    g = lt.grids_array([grid])
+    a = torch.empty((300, 300, 2), dtype=torch.float32, device="cuda")
+    e = torch.empty((300, 300), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rc = noalloc(p.data_ptr(), p.shape[1], g, a.data_ptr(), e.data_ptr(), None,
+                     torch.cuda.current_stream().cuda_stream)
+        assert rc == lt.LT_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_rejects_models_beyond_its_scratch(noalloc):
