@@ -445,10 +445,12 @@ def run_ours(a, rank, world, local):
     breakdown = {"deflect": stage_ms["deflect"], "search": stage_ms["search"],
                  "fp64_resolve": stage_ms["resolve"], "match_chi2": stage_ms["chi2"],
                  "prep_reset_and_gaps": ms_prof - seq, "step": ms_prof,
-                 "barycentres_overlapped": stage_ms["bary"],
+                 "barycentres_side_stream_latency": stage_ms["bary"],
                  "note": "the first five add up to the step (the profiled steps carry one "
-                         "event pair per stage); the barycentres run on a side stream "
-                         "during the deflection"}
+                         "event pair per stage); the barycentre kernels are issued on a side "
+                         "stream at the start of the step and run as the persistent "
+                         "deflection's blocks drain, before the search needs them: their "
+                         "latency is not part of the step's sum"}
     ms64, _, prof64, _ = timed(lt.FP64, max(1, min(a.steps, a.fp64_steps)), 1, ("deflect",))
     ms64 = max_over_ranks(ms64)
     value64 = world * 1000.0 / ms64

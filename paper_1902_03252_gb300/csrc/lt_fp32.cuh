@@ -54,7 +54,7 @@ __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, c
     const float R2 = fmaf(dy, dy, dx2);
     // rr is +inf on the centre: there the direction of alpha is undefined and
     // the bound term P rr makes the node's bound infinite (never certified)
-    const float rr = rsqrtf(R2);
+    const float rr = rsqrt_approx32(R2);
     const float ri = R2 > 0.0f ? rr : 0.0f;
     const float g = f[0].z * ri;
     AX[m] = fmaf(g, dx, AX[m]);
@@ -85,7 +85,7 @@ __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, c
     const float u = fmaf(dy, f[0].w, dxu);
     const float v = fmaf(dy, f[1].x, -dxv);
     const float R2 = fmaf(u, u, v * v);
-    const float rr = rsqrtf(R2);  // +inf on the centre: an infinite bound there
+    const float rr = rsqrt_approx32(R2);  // +inf on the centre: an infinite bound there
     const float ri = R2 > 0.0f ? rr : 0.0f;
     const float t1 = fmaf(f[1].z, u, -(f[1].w * v));
     const float t2 = fmaf(f[2].x, v, f[2].y * u);
@@ -131,15 +131,14 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
     const float x2 = xp * xp, y2 = yp * yp;
     const float t = fmaf(f[1].x, x2, y2);
     const float pa2 = t + f[1].y, ps2 = t + f[1].z;
-    ra[m] = rsqrtf(pa2);
+    ra[m] = rsqrt_approx32(pa2);
     // psi_s in one MUFU operation.  Over every float mantissa (four binades
     // checked exhaustively on GB300) sqrt.approx.ftz errs by at most 1.68 u
     // against the rounded sqrt, below the 2.71 u of ps2 * rsqrt(ps2) that the
     // error bound was derived for; psi_a keeps that form, as 1/psi_a is needed.
-    float ps;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(ps) : "f"(ps2));
+    const float ps = sqrt_approx32(ps2);
     const float pa = pa2 * ra[m];
-    const float iD = __fdividef(1.0f, pa + ps);
+    const float iD = rcp_approx32(pa + ps);
     const float dsx = fmaf(f[3].y, iD, f[3].x);
     const float dsy = fmaf(f[3].y, iD, f[3].z);
     const float px = (pa + f[2].x) * (ps + f[2].y);
@@ -147,8 +146,8 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
     const float denx = fmaf(k2, x2, px);
     const float deny = fmaf(-k2, y2, py);
     // the ds coefficients carry sig = sqrt(k2): these are sig tx, sig ty
-    tx[m] = __fdividef(xp * dsx, denx);
-    ty[m] = __fdividef(yp * dsy, deny);
+    tx[m] = (xp * dsx) * rcp_approx32(denx);
+    ty[m] = (yp * dsy) * rcp_approx32(deny);
     ux[m] = tx[m] * tx[m];
     uy[m] = ty[m] * ty[m];
     any |= (ux[m] > 1.0f) | (uy[m] > 0.25f);
@@ -156,18 +155,8 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     // the polynomials of atanc_sq32 / atanhc_sq32 on the unreduced arguments
-    float p = 7.685306482e-03f;
-    p = fmaf(p, ux[m], -3.647336364e-02f);
-    p = fmaf(p, ux[m], 8.325644583e-02f);
-    p = fmaf(p, ux[m], -1.345480382e-01f);
-    p = fmaf(p, ux[m], 1.987373084e-01f);
-    p = fmaf(p, ux[m], -3.332583010e-01f);
-    p = fmaf(p, ux[m], 9.999992251e-01f);
-    float h = 1.953562647e-01f;
-    h = fmaf(h, uy[m], 1.221839786e-01f);
-    h = fmaf(h, uy[m], 2.019458860e-01f);
-    h = fmaf(h, uy[m], 3.332709372e-01f);
-    h = fmaf(h, uy[m], 1.000000358e+00f);
+    const float p = atanc_poly32(ux[m]);
+    const float h = atanhc_poly32(uy[m]);
     px_[m] = p;
     py_[m] = h;
   }

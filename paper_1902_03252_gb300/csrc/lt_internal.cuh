@@ -189,51 +189,85 @@ __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, in
 }
 
 // ---------------------------------------------------- FP32 special functions
-// atan(t)/t of t2 = t*t >= 0: for t2 <= 1 a degree-6 polynomial in t2
-// (least-squares fit at Chebyshev nodes; relative error of its FP32 Horner
-// evaluation < 8.1e-7 = 13.5 ulp, included in the deflection's error-bound
-// coefficient errGx; the coefficients come from csrc/fit_poly.py); for t2 > 1,
-// atan(t) = pi/2 -
-// atan(1/t) gives (pi/2)/t - P(1/t2)/t2 with one MUFU rsqrt.  The range test
-// is a real branch: the 32 nodes of a warp see one potential from nearly the
-// same direction, so it is almost always uniform.
-//
-// atanh(t)/t of t2 = t*t in [0, 1): for t2 <= 1/4 a degree-4 polynomial in
-// t2 (same fit; relative error < 4.6e-7 = 7.7 ulp, included in errGy); above,
-// atanh(t) = ln((1+t)/(1-t))/2
-// with MUFU rsqrt, rcp and lg2 (the ratio is >= 3 there, where lg2 has a
-// 2-ulp relative error).
-__device__ __forceinline__ float atanc_sq32(float t2) {
-  float p, inv = 0.f, r = 0.f;
-  float u = t2;
-  if (t2 > 1.0f) {
-    r = rsqrtf(t2);
-    inv = r * r;
-    u = inv;
-  }
-  p = 7.685306482e-03f;
+// The hardware approximations the FP32 path uses, named by their PTX
+// instructions (flush-to-zero forms).  Their largest relative errors are
+// measured exhaustively on the GPU over every input the path can give them
+// (tests/test_gpu_special.py) and enter the error bound through those
+// measured maxima.
+__device__ __forceinline__ float rsqrt_approx32(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx32(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_approx32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx32(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Polynomials in u = t*t, evaluated by Horner's rule with fused
+// multiply-adds: atan(t)/t on 0 <= u <= 1 (degree 6) and atanh(t)/t on
+// 0 <= u <= 1/4 (degree 4).  Least-squares fits in the relative sense at
+// Chebyshev nodes (csrc/fit_poly.py).  The relative errors of these FP32
+// evaluations against the exact functions, taken over every float u of the
+// two intervals (tests/test_fp32_poly.py), are 13.5 and 7.7 ulp.  These
+// literals are the single copy of the coefficients.
+__device__ __forceinline__ float atanc_poly32(float u) {
+  float p = 7.685306482e-03f;
   p = fmaf(p, u, -3.647336364e-02f);
   p = fmaf(p, u, 8.325644583e-02f);
   p = fmaf(p, u, -1.345480382e-01f);
   p = fmaf(p, u, 1.987373084e-01f);
   p = fmaf(p, u, -3.332583010e-01f);
   p = fmaf(p, u, 9.999992251e-01f);
-  if (t2 > 1.0f) p = fmaf(1.57079633f, r, -(p * inv));
   return p;
+}
+__device__ __forceinline__ float atanhc_poly32(float u) {
+  float p = 1.953562647e-01f;
+  p = fmaf(p, u, 1.221839786e-01f);
+  p = fmaf(p, u, 2.019458860e-01f);
+  p = fmaf(p, u, 3.332709372e-01f);
+  p = fmaf(p, u, 1.000000358e+00f);
+  return p;
+}
+
+// atan(t)/t of t2 = t*t >= 0: the polynomial for t2 <= 1; for t2 > 1,
+// atan(t) = pi/2 - atan(1/t) gives (pi/2)/t - P(1/t2)/t2 with one rsqrt.
+// The range test is a real branch: the 32 nodes of a warp see one potential
+// from nearly the same direction, so it is almost always uniform.
+//
+// atanh(t)/t of t2 = t*t in [0, 1): the polynomial for t2 <= 1/4; above,
+// atanh(t) = ln((1+t)/(1-t))/2 with rsqrt, rcp and lg2 (the ratio is >= 3
+// there, away from lg2's absolute-error range around 1).
+// The largest relative errors of both functions over all their float
+// arguments are measured on the GPU (tests/test_gpu_special.py).
+__device__ __forceinline__ float atanc_sq32(float t2) {
+  if (t2 > 1.0f) {
+    const float r = rsqrt_approx32(t2);
+    const float inv = r * r;
+    const float p = atanc_poly32(inv);
+    return fmaf(1.57079633f, r, -(p * inv));
+  }
+  return atanc_poly32(t2);
 }
 __device__ __forceinline__ float atanhc_sq32(float t2) {
   if (t2 > 0.25f) {
     t2 = fminf(t2, 0.99999988f);
-    const float r = rsqrtf(t2);
+    const float r = rsqrt_approx32(t2);
     const float t = t2 * r;
-    return __log2f(__fdividef(1.0f + t, 1.0f - t)) * (0.5f * 0.693147181f) * r;
+    return lg2_approx32((1.0f + t) * rcp_approx32(1.0f - t)) * (0.5f * 0.693147181f) * r;
   }
-  float p = 1.953562647e-01f;
-  p = fmaf(p, t2, 1.221839786e-01f);
-  p = fmaf(p, t2, 2.019458860e-01f);
-  p = fmaf(p, t2, 3.332709372e-01f);
-  p = fmaf(p, t2, 1.000000358e+00f);
-  return p;
+  return atanhc_poly32(t2);
 }
 
 // Launch-shape variants of the FP32 deflection kernel (autotuned).
