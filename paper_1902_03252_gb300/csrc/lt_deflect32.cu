@@ -10,8 +10,6 @@
 
 namespace lt {
 
-constexpr int kChunk32 = 256;  // potentials staged in shared memory at a time
-
 // --------------------------------------------------------------- deflection
 // MINB: the resident blocks per SM the register allocation must allow (left
 // to the compiler, the (256, 4) shape is squeezed into 64 registers and spills)
@@ -48,66 +46,17 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
     // node coordinates rounded once from FP64: error u|theta| (App. A's
     // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
     const float X = (float)(g.x0 + (double)i * g.dx);
-    float Y[NPT], AX[NPT], AY[NPT], PX[NPT], PY[NPT], ER[NPT];
+    float Y[NPT], AX[NPT], AY[NPT], ER[NPT];
 #pragma unroll
-    for (int m = 0; m < NPT; ++m) {
-      PX[m] = 0.0f;
-      PY[m] = 0.0f;
-      Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
-      AX[m] = 0.0f;
-      AY[m] = 0.0f;
-      ER[m] = 0.0f;
-    }
-    const float theta1 = g.theta_max;
-    const Pot32* pb = pot32 + (int64_t)b * n_pot;
-    for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
-      const int cn = min(kChunk32, n_pot - c0);
-      __syncthreads();
-      for (int v = threadIdx.x; v < cn * 5; v += NT) {
-        int k = v / 5, w = v - k * 5;
-        float4 val = pb[c0 + k].f[w];
-        if (w == 4) {  // translation-error coefficient for this grid
-          float4 h = pb[c0 + k].f[0];
-          // strictly positive, so that P times an infinite 1/R (a node on an
-          // SIS/SIE centre) is +inf, never NaN, even for a zero-mass potential
-          val.x = fmaf(val.x, theta1 + fabsf(h.x) + fabsf(h.y), 1e-30f);
-        }
-        sp[v] = val;
-      }
-      __syncthreads();
-      // kind segments [0, n_sis) SIS, [n_sis, n_sis + n_piemd) PIEMD, rest SIE
-      const int e_sis = min(max(sg.n_sis - c0, 0), cn);
-      const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
-      // groups of at most kSumGroup potentials of one kind segment, each
-      // summed into PX, PY and then added to the totals
-      for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
-        for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k) {
-          const float4* f = &sp[k * 5];
-          sis32_nodes<NPT>(f, f[4].x, X, Y, PX, PY, ER);
-        }
-        flush_group<NPT>(AX, AY, PX, PY, ER);
-      }
-      for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
-        for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k) {
-          const float4* f = &sp[k * 5];
-          piemd32_nodes<NPT>(f, f[4].x, X, Y, PX, PY, ER);
-        }
-        flush_group<NPT>(AX, AY, PX, PY, ER);
-      }
-      for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
-        for (int k = k0; k < min(k0 + kSumGroup, cn); ++k) {
-          const float4* f = &sp[k * 5];
-          sie32_nodes<NPT>(f, f[4].x, X, Y, PX, PY, ER);
-        }
-        flush_group<NPT>(AX, AY, PX, PY, ER);
-      }
-    }
+    for (int m = 0; m < NPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
+    deflect32_nodes<NT, NPT>(pot32 + (int64_t)b * n_pot, n_pot, sg, g.theta_max, X, Y, sp, AX,
+                             AY, ER);
     const float qs = sg.q_tot;
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
       if (live && j0 + m < g.ny)
         node_out[g.node_off + (int64_t)(j0 + m) * g.nx + i] =
-            make_float4(AX[m], AY[m], node_bound(ER[m] + qs), 0.0f);
+            make_float4(AX[m], AY[m], node_bound(__fadd_ru(ER[m], qs)), 0.0f);
     }
   }
 }

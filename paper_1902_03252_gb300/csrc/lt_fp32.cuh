@@ -25,6 +25,28 @@ namespace lt {
 // error itself.
 constexpr int kSumGroup = 32;
 
+// The bound's terms are accumulated with upward rounding (__fmaf_ru,
+// __fadd_ru), so that the float sums never fall below the exact sums of the
+// terms; the terms themselves are derived in k_prep.
+
+// Coefficient P of the per-node term P / d of one potential (units of u) on a
+// grid whose largest |node coordinate| is theta1: errP0 W, W = theta1 + |cx| +
+// |cy|, and for the PIEMD the factor of the segment between the exact and the
+// rounded node: 1 / (1 - x) for x = 14.18 (1 + 3u) u W / (q a) <= 1/2, else
+// 10.03 max(1, x) (see k_prep).  Rounded up throughout; strictly positive, so
+// that P times an infinite 1/d (a node on an SIS/SIE centre) is +inf, never
+// NaN, even for a zero-mass potential.
+__device__ __forceinline__ float stage_p32(const Pot32& r, bool piemd, float theta1) {
+  const float W = __fadd_ru(__fadd_ru(theta1, fabsf(r.f[0].x)), fabsf(r.f[0].y));
+  float P = __fmul_ru(r.f[4].x, W);
+  if (piemd) {
+    const float qa = __fsqrt_rd(__fmul_rd(r.f[2].x, r.f[2].z));  // q a, rounded down
+    const float xk = __fdiv_ru(__fmul_ru(8.4521e-7f, W), qa);   // 14.18 (1 + 3u) u, rounded up
+    P = xk <= 0.5f ? __fdiv_ru(P, __fsub_rd(1.0f, xk)) : __fmul_ru(P, __fmul_ru(10.03f, fmaxf(1.0f, xk)));
+  }
+  return __fadd_ru(P, 1e-30f);
+}
+
 // Add a group's partial sums to the totals (one rounding per component,
 // bounded by the new total) and clear them.
 template <int NPT>
@@ -34,7 +56,7 @@ __device__ __forceinline__ void flush_group(float* AX, float* AY, float* PX, flo
   for (int m = 0; m < NPT; ++m) {
     AX[m] += PX[m];
     AY[m] += PY[m];
-    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
     PX[m] = 0.0f;
     PY[m] = 0.0f;
   }
@@ -59,8 +81,8 @@ __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, c
     const float g = f[0].z * ri;
     AX[m] = fmaf(g, dx, AX[m]);
     AY[m] = fmaf(g, dy, AY[m]);
-    ER[m] = fmaf(P, rr, ER[m]);
-    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    ER[m] = __fmaf_ru(P, rr, ER[m]);
+    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
   }
 }
 
@@ -91,8 +113,8 @@ __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, c
     const float t2 = fmaf(f[2].x, v, f[2].y * u);
     AX[m] = fmaf(ri, t1, AX[m]);
     AY[m] = fmaf(ri, t2, AY[m]);
-    ER[m] = fmaf(P, rr, ER[m]);
-    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    ER[m] = __fmaf_ru(P, rr, ER[m]);
+    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
   }
 }
 
@@ -174,9 +196,75 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
     const float gy = ty[m] * py_[m];
     AX[m] = fmaf(gx, Bc, fmaf(-gy, Bs, AX[m]));
     AY[m] = fmaf(gy, Bc, fmaf(gx, Bs, AY[m]));
-    ER[m] = fmaf(P, ra[m], ER[m]);
-    ER[m] = fmaf(f[4].y, fabsf(gx), fmaf(f[4].z, fabsf(gy), ER[m]));
-    ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    ER[m] = __fmaf_ru(P, ra[m], ER[m]);
+    ER[m] = __fmaf_ru(f[4].y, fabsf(gx), __fmaf_ru(f[4].z, fabsf(gy), ER[m]));
+    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
+  }
+}
+
+// Potentials staged in shared memory at a time by the deflection kernels.
+constexpr int kChunk32 = 256;
+
+// Stage potentials [c0, c0 + cn) of a sample's records into shared memory,
+// f[4].x replaced by the grid's coefficient P (stage_p32).  Called by all NT
+// threads of the block.
+template <int NT>
+__device__ __forceinline__ void stage_chunk32(float4* sp, const Pot32* __restrict__ pb, int c0,
+                                              int cn, const Seg32& sg, float theta1) {
+  for (int v = threadIdx.x; v < cn * 5; v += NT) {
+    const int k = v / 5, w = v - k * 5;
+    float4 val = pb[c0 + k].f[w];
+    if (w == 4) {
+      const int kk = c0 + k;
+      val.x = stage_p32(pb[kk], kk >= sg.n_sis && kk < sg.n_sis + sg.n_piemd, theta1);
+    }
+    sp[v] = val;
+  }
+}
+
+// The per-item body of both FP32 deflection kernels: the deflection (AX, AY)
+// and the running-bound terms ER of one thread's NPT nodes (column X, rows
+// Y[]) over all n_pot potentials of one sample, kind segment by kind segment
+// ([0, n_sis) SIS, then PIEMD, then SIE), in groups of at most kSumGroup
+// potentials whose partial sums join the totals once per group.  The order of
+// every operation of a node depends only on the potentials, not on NT or NPT.
+// sp: shared memory of kChunk32 * 5 float4; called by all NT threads.
+template <int NT, int NPT>
+__device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, int n_pot,
+                                                const Seg32& sg, float theta1, float X,
+                                                const float* Y, float4* sp, float* AX,
+                                                float* AY, float* ER) {
+  float PX[NPT], PY[NPT];
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    PX[m] = 0.0f;
+    PY[m] = 0.0f;
+    AX[m] = 0.0f;
+    AY[m] = 0.0f;
+    ER[m] = 0.0f;
+  }
+  for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
+    const int cn = min(kChunk32, n_pot - c0);
+    __syncthreads();  // the previous chunk's (or item's) readers of sp are done
+    stage_chunk32<NT>(sp, pb, c0, cn, sg, theta1);
+    __syncthreads();
+    const int e_sis = min(max(sg.n_sis - c0, 0), cn);
+    const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
+    for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
+      for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k)
+        sis32_nodes<NPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+      flush_group<NPT>(AX, AY, PX, PY, ER);
+    }
+    for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
+      for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k)
+        piemd32_nodes<NPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+      flush_group<NPT>(AX, AY, PX, PY, ER);
+    }
+    for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
+      for (int k = k0; k < min(k0 + kSumGroup, cn); ++k)
+        sie32_nodes<NPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+      flush_group<NPT>(AX, AY, PX, PY, ER);
+    }
   }
 }
 

@@ -121,26 +121,68 @@ __global__ void __launch_bounds__(kPrepThreads)
     Pot32 f;
     for (int w = 0; w < 5; ++w) f.f[w] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float cx = (float)p.cx, cy = (float)p.cy, c = (float)p.c, s = (float)p.s;
-    // First-order error-bound coefficients (units of the FP32 unit roundoff):
-    // errP0 * (4 Theta + |c|) / R-like distance covers the rounding of the
-    // node coordinates, the centre and the translation, carried through the
-    // deflection's spatial derivatives; errGx/errGy the relative rounding of
-    // the rotated-frame components; errQ the distance-proportional rounding
-    // of translation and rotation carried through the same derivatives.
+    // Coefficients of the FP32 running error bound, in units of u = 2^-24
+    // (every constant below is rounded up to float).  The bound of a node is
+    //   E = (1 + 2^-16) u [ sum_k P_k / d_k + sum_k (Gx_k |gx_k| + Gy_k |gy_k|)
+    //                       + sum_k Q_k + summation terms ],
+    // d_k the node's FP32 distance measure to potential k (|theta - c| for the
+    // SIS, R for the SIE, psi_a for the PIEMD).  It bounds both components
+    // of |alpha_FP32 - alpha|, alpha the exact deflection at the FP64 node
+    // position with the FP64 parameters.  Derivation, term by term:
+    //  * input errors: the node coordinate (rounded once from FP64), the
+    //    centre and the translation err by at most 2u(1+u)(Theta + |c_x|) per
+    //    coordinate, W = Theta + |c_x| + |c_y|; the rotation (two rounded
+    //    coefficients, one product, one FMA) adds 4.01 u |Delta|_1, Delta the
+    //    translated node.  They move the deflection by at most
+    //    |J|_2 |e|_2, J its Jacobian along the segment between the exact and
+    //    the rounded rotated node: P / d carries the W part, Q the |Delta| part;
+    //  * evaluation errors: relative errors of the rotated-frame components,
+    //    counted operation by operation (each rounding one u, the hardware
+    //    approximations and special functions their measured maxima kEps*),
+    //    as coefficients G of |g| (PIEMD) or, when |alpha_k| is bounded by a
+    //    constant, folded into Q (SIS, SIE);
+    //  * accumulation: every fused step errs by at most u (2 + u) max|partial|,
+    //    charged per node by the 2 (|PX| + |PY|) and 2 (|AX| + |AY|) terms of
+    //    the kernel;
+    //  * second order: counted units n enter as gamma(n) = n / (1 - n u)
+    //    (Higham, Accuracy and Stability of Numerical Algorithms, Lemma 3.1).
+    const double U = kU32d;
+    auto gam = [U](double n) { return n * U >= 0.25 ? 1e30 : n / (1.0 - n * U); };
     double Q;
     if (kind == LT_SIS) {
+      // Jacobian of b0 n(Delta): b0/|Delta| (2-norm).  Where |D| >= 2|e|:
+      // error <= 2 b0 |e| / |D| with |e| <= u(1+u)(W2 + |Delta|), W2 =
+      // 2 Theta + |c_x| + |c_y| <= 2 W: P = 4 b0 W, and the |Delta| part
+      // (|Delta| <= 1.5 |D|) gives 3 b0 in Q.  Where |D| < 2|e| the error is
+      // at most 2 b0 (two vectors of length b0), which P / |D| covers with
+      // P >= 4 b0 |e| / u: P = 8 b0 W.  rr = rsqrt(R2) errs by (1.01 + eps_r) u.
+      // Evaluation: b0 (1 u), R2 (2 u, halved by the root), rsqrt, b0 * rr
+      // (1 u): 3 + eps_r relative, |alpha_k| <= b0, into Q.
+      const double p0 = 8.0 * p.b0 * (1.0 + U) / ((1.0 - 3.1 * U) * (1.0 - (1.01 + kEpsRsqrt) * U));
       f.f[0] = make_float4(cx, cy, (float)p.b0, 0.f);
-      f.f[4] = make_float4((float)(2.0 * p.b0), 0.f, 0.f, 0.f);
-      Q = 8.0 * p.b0;
+      f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
+      Q = p.b0 * (gam(3.0 + kEpsRsqrt) + 3.0 * (1.0 + 3.0 * U));
     } else if (kind == LT_SIE) {
-      const double ge = (1.0 + p.e) / (1.0 - p.e);
       const double r1 = sqrt(1.0 - p.e), r2 = sqrt(1.0 + p.e);
+      // z = (r1 x', r2 y'), g = b0 diag(r1, r2) z / |z|: Jacobian in z at most
+      // b0 r2 / |z|; the input error in z is at most sqrt(2) u (1+3u)
+      // (W2 + 4.01 |Delta|_1) (r1^2 + r2^2 = 2).  Where |z| >= 2|e_z|: the W
+      // part gives P = 2 sqrt(2) b0 r2 W2 <= 5.66 b0 r2 W and the |Delta| part
+      // (|Delta|_1 <= sqrt(2) |z| / r1 (1 + ...)) Q = 16.04 b0 r2 / r1; where
+      // |z| < 2 |e_z| (then |Delta|_1 < 2 sqrt(2) |e_z| / r1) the error is at
+      // most 2 b0 r2, covered by P = 4 sqrt(2) b0 r2 W2 / (1 - 16.04 u / r1)
+      // <= 11.32 b0 r2 W / (...).  Evaluation of t = b0 R(-phi) (r1 u, r2 v):
+      // three roundings on each product term, |t| <= b0 r2 R, so
+      // |t_FP32 - t| <= 3 sqrt(2) u b0 r2 R; times rr ((1.01 + eps_r) u):
+      // (5.25 + eps_r) b0 r2 into Q.
+      const double p0 = 11.32 * p.b0 * r2 * (1.0 + 3.0 * U) /
+                        ((1.0 - 16.1 * U / r1) * (1.0 - (1.01 + kEpsRsqrt) * U));
       f.f[0] = make_float4(cx, cy, (float)(r1 * p.c), (float)(r1 * p.s));
       f.f[1] = make_float4((float)(r2 * p.c), (float)(r2 * p.s), (float)(p.b0 * r1 * p.c),
                            (float)(p.b0 * r2 * p.s));
       f.f[2] = make_float4((float)(p.b0 * r2 * p.c), (float)(p.b0 * r1 * p.s), 0.f, 0.f);
-      f.f[4] = make_float4((float)(4.0 * p.b0 * ge), 0.f, 0.f, 0.f);
-      Q = 16.0 * p.b0 * ge;
+      f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
+      Q = p.b0 * r2 * (gam(5.25 + kEpsRsqrt) + 16.04 * (1.0 + 3.0 * U) / r1);
     } else {
       const double a = p.a, sc = p.sc, q2 = p.q2, q = p.q;
       const double B = p.scale;
@@ -155,19 +197,57 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[2] = make_float4((float)a, (float)sc, (float)(q2 * a), (float)(q2 * sc));
       f.f[3] = make_float4((float)(sig * (sc - a)), (float)(sig * q2 * (sc + a) * (sc - a)),
                            (float)(sig * q2 * (sc - a)), (float)(Bs * p.c));
+      // Evaluation at the rounded rotated node (x, y), relative errors in u
+      // (each record constant, product, sum and FMA one u; sums of positive
+      // terms keep the larger relative error):
+      //   psi_a^2, psi_s^2: 4; pa = psi_a: 3 + eps_r (rsqrt, times psi_a^2);
+      //   ps: 2 + eps_s; 1/(pa + ps): m7 = 4 + max(eps_r, eps_s - 1) + eps_rcp;
+      //   ds_x, ds_y: m7 + 2; (pa + a)(ps + s), (pa + q2 a)(ps + q2 s):
+      //   8 + eps_r + eps_s; den_x (a sum of positive terms): 9 + eps_r + eps_s;
+      //   den_y = p_y - k2 y^2 >= q^2 p_y (y^2 <= psi_a psi_s <= p_y), so
+      //   (8 + eps_r + eps_s + 2 k2)/q^2 + 1; t_x = x ds_x rcp(den_x):
+      //   n_tx = m7 + 13 + eps_r + eps_s + eps_rcp; t_y: n_ty = m7 + 4 +
+      //   eps_rcp + that of den_y.
+      //   g_x = atan(t_x): elasticity of atan <= 1, the rounded square 1 u at
+      //   elasticity <= 1/2, the special function eps_atanc, the product 1 u;
+      //   g_y = atanh(t_y): elasticity <= 1/(1 - t_y^2) <= 1/q^2 (|t_y| < k),
+      //   the square at k2/(2 q^2), eps_atanhc, 1 u.  Two more units for the
+      //   rounded (Bc, Bs) and the inner FMA of the accumulation.
+      const double m7 = 4.0 + fmax(kEpsRsqrt, kEpsSqrt - 1.0) + kEpsRcp;
+      const double n_tx = m7 + 13.0 + kEpsRsqrt + kEpsSqrt + kEpsRcp;
       const double iq2 = 1.0 / q2;
-      // the polynomial errors of atanc / atanhc (13.5 and 7.7 ulp) are part
-      // of errGx and errGy
-      const double gy = (14.0 + 17.0 * iq2) * (1.0 + iq2) + 16.0;
-      f.f[4] = make_float4((float)(4.0 * B / q), (float)(92.0 * Bs), (float)(gy * Bs),
-                           (float)(Bs * p.s));
-      Q = 16.0 * B * iq2;
+      const double c_dy = (8.0 + kEpsRsqrt + kEpsSqrt + 2.0 * p.k2) * iq2 + 1.0;
+      const double n_ty = m7 + 4.0 + kEpsRcp + c_dy;
+      // q < 0.01 (e > 0.99): the atan argument (below 1/q) leaves the range
+      // over which kEpsAtanc is measured, and the bound is not finite
+      const double Gx = q < 0.01 ? 1e30 : gam(n_tx + kEpsAtanc + 3.5);
+      // 1/(q^2 - 3 n_ty u): the elasticity along the perturbed path
+      const double el = 1.0 / fmax(q2 - 3.0 * n_ty * U, 1e-300);
+      // atanh(t)/t: the polynomial's error, or the logarithm's divided by
+      // 1 - t_y^2 >= q^2 - 3 n_ty u
+      const double eps_h = fmax(kEpsAtanhc, kEpsAtanhcLog * el);
+      const double Gy = q < 0.01 ? 1e30 : gam(n_ty * el + 0.5 * p.k2 * el + eps_h + 3.0);
+      // Input errors (rotated frame, 2-norm): |e'| <= sqrt(2) u (1+3u)
+      // (W2 + 4.01 |Delta|_1), W2 <= 2 W.  The Jacobian of the dPIE in the
+      // rotated frame, per unit B, is H_a - H_s with H_w positive
+      // semidefinite of trace 1/psi_w, so |H|_2 <= 1/psi_a, and psi_a has
+      // gradient norm <= 1 and psi_a >= q a, psi_a >= q |Delta|.  With
+      // x_k = 14.18 (1+3u) u W / (q a) (>= |e'| / psi_a): if x_k <= 1/2 the W
+      // part gives P = 2 sqrt(2) B W / (1 - x_k) (staging applies the
+      // factor; errP0 = 2 sqrt(2) B (1+3u) / (1 - (2 + eps_r) u), ra errs by
+      // (2 + eps_r) u) and the |Delta| part Q = 16.04 B / q; otherwise P =
+      // 28.36 B W max(1, x_k) covers all input errors (stage_p32).
+      const double p0 = 2.8285 * B * (1.0 + 3.0 * U) / (1.0 - (2.0 + kEpsRsqrt) * U);
+      f.f[4] = make_float4(__double2float_ru(p0), __double2float_ru(Gx * Bs),
+                           __double2float_ru(Gy * Bs), (float)(Bs * p.s));
+      Q = 16.04 * (1.0 + 3.0 * U) * B / q;
     }
-    qsum += (float)Q;
+    qsum = __fadd_ru(qsum, __double2float_ru(Q));
     pot32[(int64_t)b * n_pot + rank] = f;
   }
-  // sum of the static bound terms: fixed order (warp butterflies, then warps)
-  for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, o);
+  // sum of the static bound terms (rounded up): fixed order (warp
+  // butterflies, then warps)
+  for (int o = 16; o > 0; o >>= 1) qsum = __fadd_ru(qsum, __shfl_xor_sync(0xffffffffu, qsum, o));
   if (lane == 0) qpart[wid] = qsum;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -45,28 +45,45 @@ static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 //           f[3] = {sig(s-a), sig q2(s+a)(s-a), sig q2(s-a), (B/sig) c};
 //           f[4] = {errP0, errGx B/sig, errGy B/sig, (B/sig) s}, sig = sqrt(k2)
 //   SIS/SIE: f[4] = {errP0, 0, 0, 0}
-// (error-bound coefficients errP0, errGx, errGy; the static terms errQ are
-// summed into Seg32::q_tot)
-// errP0 * (Theta + |cx| + |cy|) is the translation-error coefficient of the
-// running bound (Theta = largest |node coordinate| of the grid; node
-// coordinates are rounded once from FP64).
+// (error-bound coefficients errP0, errGx, errGy, in units of u; the static
+// terms errQ are summed into Seg32::q_tot).  At staging, errP0 times
+// W = Theta + |cx| + |cy| (Theta = largest |node coordinate| of the grid; node
+// coordinates are rounded once from FP64) becomes the coefficient P of the
+// per-node term P / distance (stage_p32); see k_prep for the derivation of
+// every coefficient.
 struct Pot32 {
   float4 f[5];
 };
 static_assert(sizeof(Pot32) == 80, "Pot32 layout");
 
-// Safety factor applied to the first-order running error bound of every
-// node: the bound's terms are first order in the unit roundoff, so any factor
-// above 1 covers the neglected second-order terms; 1.25 also leaves room for
-// a coefficient underestimated by a quarter.  (Observed: the largest ratio of
-// actual error to bound over all test grids is below 0.05.)
-constexpr float kBoundSafety = 1.25f;
+// ------------------------------------------------ FP32 error-bound constants
+// Largest relative errors, in units of the FP32 unit roundoff u = 2^-24, of
+// the FP32 primitives of the deflection: the hardware approximations and the
+// library's atan(t)/t and atanh(t)/t (polynomials with range reduction), each
+// measured at every float argument the kernels can give it
+// (tests/test_gpu_special.py; tests/test_fp32_poly.py for the polynomials
+// alone).  Those tests fail if a measurement exceeds the value here, so the
+// bound's coefficients, derived from these values in k_prep, stay valid.
+// For atanh(t)/t above u = 1/4 the relative error grows like 1/(1 - u) (the
+// logarithm's argument (1 + t)/(1 - t) inherits the rounding of t): the
+// constant is the largest (1 - u) times the relative error, and the bound
+// divides it by its own lower bound on 1 - u (1 - t^2 > q^2).
+constexpr double kEpsRsqrt = 2.1;       // rsqrt.approx.ftz.f32 (measured 2.092)
+constexpr double kEpsSqrt = 1.7;        // sqrt.approx.ftz.f32 (1.678)
+constexpr double kEpsRcp = 1.7;         // rcp.approx.ftz.f32 (1.649)
+constexpr double kEpsAtanc = 13.6;      // atanc_sq32 on [0, 2^14] (13.500)
+constexpr double kEpsAtanhc = 7.7;      // atanhc_sq32 on [0, 1/4] (7.574)
+constexpr double kEpsAtanhcLog = 5.0;   // (1 - u) x atanhc_sq32 on [1/4, 0.99999988] (4.917)
+constexpr double kU32d = 5.9604644775390625e-8;  // u as a double
 
-// A node's bound from its accumulated terms (in units of the unit roundoff),
-// capped at 1e30: a node on an SIS/SIE centre has an infinite term, and a
-// finite cap keeps every later product (r E with r = 0 included) a number.
+// A node's bound from its accumulated terms (units of u, accumulated with
+// upward rounding).  The factor 1 + 2^-16 covers the terms of second order
+// in u that the coefficients leave out (the FP64 rounding of the record
+// constants, the 2 + u of a fused accumulation step).  Capped at 1e30: a node
+// on an SIS/SIE centre has an infinite term, and a finite cap keeps every
+// later product (r E with r = 0 included) a number.
 __device__ __forceinline__ float node_bound(float terms) {
-  return fminf(kBoundSafety * kU32 * terms, 1e30f);
+  return fminf(__fmul_ru(__fmul_ru(kU32, 1.0000152587890625f), terms), 1e30f);
 }
 
 // Per-sample kind segments of the FP32 records: [n_sis, n_piemd, n_sie, 0]

@@ -61,14 +61,14 @@ lt_status device_setup(int dev, unsigned char** base, int* sms) {
 // registers for 3 resident blocks per SM
 constexpr int kNT = 256, kNPT = 4, kMinBlocks = 3;
 
-// Same arithmetic as the batched deflection kernel (same per-potential
-// functions, kind segments and order), for one sample, writing alpha and the
-// running error bound straight into the caller's buffers.
+// The batched deflection kernel's per-item body (deflect32_nodes) for one
+// sample, writing alpha and the running error bound straight into the
+// caller's buffers.
 __global__ void __launch_bounds__(kNT, kMinBlocks)
     k_deflect32_noalloc(const Pot32* __restrict__ pot32, const Seg32* __restrict__ seg, int n_pot,
                         SampleGrid g, int64_t n_items, float2* __restrict__ alpha,
                         float* __restrict__ err) {
-  __shared__ float4 sp[256 * 5];
+  __shared__ float4 sp[kChunk32 * 5];
   const Seg32 sg = *seg;
   const int64_t bands = ((int64_t)g.ny + kNPT - 1) / kNPT;
   const float theta1 = g.theta_max;
@@ -83,56 +83,17 @@ __global__ void __launch_bounds__(kNT, kMinBlocks)
     // node coordinates rounded once from FP64: error u|theta| (App. A's
     // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
     const float X = (float)(g.x0 + (double)i * g.dx);
-    float Y[kNPT], AX[kNPT], AY[kNPT], PX[kNPT], PY[kNPT], ER[kNPT];
+    float Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
 #pragma unroll
-    for (int m = 0; m < kNPT; ++m) {
-      PX[m] = 0.0f;
-      PY[m] = 0.0f;
-      Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
-      AX[m] = 0.0f;
-      AY[m] = 0.0f;
-      ER[m] = 0.0f;
-    }
-    for (int c0 = 0; c0 < n_pot; c0 += 256) {
-      const int cn = min(256, n_pot - c0);
-      __syncthreads();
-      for (int v = threadIdx.x; v < cn * 5; v += kNT) {
-        const int k = v / 5, w = v - k * 5;
-        float4 val = pot32[c0 + k].f[w];
-        if (w == 4) {
-          const float4 h = pot32[c0 + k].f[0];
-          // strictly positive, so that P times an infinite 1/R (a node on an
-          // SIS/SIE centre) is +inf, never NaN, even for a zero-mass potential
-          val.x = fmaf(val.x, theta1 + fabsf(h.x) + fabsf(h.y), 1e-30f);
-        }
-        sp[v] = val;
-      }
-      __syncthreads();
-      const int e_sis = min(max(sg.n_sis - c0, 0), cn);
-      const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
-      // the batched kernel's groups of kSumGroup potentials per kind segment
-      for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
-        for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k)
-          sis32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-        flush_group<kNPT>(AX, AY, PX, PY, ER);
-      }
-      for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
-        for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k)
-          piemd32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-        flush_group<kNPT>(AX, AY, PX, PY, ER);
-      }
-      for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
-        for (int k = k0; k < min(k0 + kSumGroup, cn); ++k)
-          sie32_nodes<kNPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-        flush_group<kNPT>(AX, AY, PX, PY, ER);
-      }
-    }
+    for (int m = 0; m < kNPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
+    // the batched kernel's body: the same operations in the same order
+    deflect32_nodes<kNT, kNPT>(pot32, n_pot, sg, theta1, X, Y, sp, AX, AY, ER);
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {
       if (live && j0 + m < g.ny) {
         const int64_t n = (int64_t)(j0 + m) * g.nx + i;
         alpha[n] = make_float2(AX[m], AY[m]);
-        if (err) err[n] = node_bound(ER[m] + sg.q_tot);
+        if (err) err[n] = node_bound(__fadd_ru(ER[m], sg.q_tot));
       }
     }
   }

@@ -19,11 +19,35 @@ struct SrcSmem {
   float px, py, r, mu0;  // mu0 = u (4 Theta + |px| + |py|) (input rounding)
 };
 
+// 2u(1 + u) rounded up: the FP32 rounding of an edge function a x b =
+// fma(ax, by, -(ay bx)) is at most u |ay bx| + u |result| <= 2u(1 + u)
+// (|ax by| + |ay bx|).
+__device__ __forceinline__ float u2_up() { return __int_as_float(0x34000001); }
+
+// Bound on |a x b - a* x b*| for vertices a, b (relative to the source, FP32)
+// whose coordinates are within ma, mb of the exact a*, b*: the input part
+// ma |b|_1 + mb |a|_1 + 2 ma mb and the rounding of the FP32 edge function.
+// Rounded up throughout.
+__device__ __forceinline__ float edge_bound(float ax, float ay, float bx, float by, float ma,
+                                            float mb) {
+  const float la = __fadd_ru(fabsf(ax), fabsf(ay)), lb = __fadd_ru(fabsf(bx), fabsf(by));
+  const float rnd = __fmul_ru(u2_up(), __fadd_ru(__fmul_ru(fabsf(ax), fabsf(by)),
+                                                 __fmul_ru(fabsf(ay), fabsf(bx))));
+  return __fmaf_ru(ma, lb, __fmaf_ru(mb, la, __fmaf_ru(__fmul_ru(2.0f, ma), mb, rnd)));
+}
+
 // Classify one triangle with relative vertices a, b, c (vertex - source,
 // FP32) and per-vertex error bounds m[3].  Returns 0 = certainly outside,
-// 1 = certainly inside, 2 = undecided.  On 1, w[] receives the weights and
-// *pos_err a bound on the position error of the interpolated image
-// (in units of the cell size).
+// 1 = certainly inside, 2 = undecided.  An edge function whose magnitude
+// exceeds its bound has the sign of the exact one; the triangle is certainly
+// outside if two edge functions certainly differ in sign, certainly inside if
+// all three certainly agree (then no tie rule applies).  On 1, w[] receives
+// the weights and *pos_err a bound on the interpolated image's position
+// error in units of the cell size: the weights w_v = e_v / det err by at most
+// (E_v + w_v sE') / (|det| - sE'), sE' the edge bounds plus the rounding of
+// det = e0 + e1 + e2, and by 2u in their own rounding; the image position
+// A + w_B (B - A) + w_C (C - A), |B - A|, |C - A| <= h per coordinate, then
+// errs by at most h (|dw_B| + |dw_C|) <= h (2 sE' / (|det| - sE') + 4u).
 __device__ __forceinline__ int classify32(float ax, float ay, float bx, float by, float cx,
                                           float cy, float ma, float mb, float mc, float w[3],
                                           float* pos_err) {
@@ -31,11 +55,9 @@ __device__ __forceinline__ int classify32(float ax, float ay, float bx, float by
   float e0 = fmaf(ax, by, -(ay * bx));
   float e1 = fmaf(bx, cy, -(by * cx));
   float e2 = fmaf(cx, ay, -(cy * ax));
-  const float u2 = 2.0f * kU32;
-  float la = fabsf(ax) + fabsf(ay), lb = fabsf(bx) + fabsf(by), lc = fabsf(cx) + fabsf(cy);
-  float E0 = 1.25f * (ma * lb + mb * la + 2.0f * ma * mb + u2 * (fabsf(ax * by) + fabsf(ay * bx)));
-  float E1 = 1.25f * (mb * lc + mc * lb + 2.0f * mb * mc + u2 * (fabsf(bx * cy) + fabsf(by * cx)));
-  float E2 = 1.25f * (mc * la + ma * lc + 2.0f * mc * ma + u2 * (fabsf(cx * ay) + fabsf(cy * ax)));
+  const float E0 = edge_bound(ax, ay, bx, by, ma, mb);
+  const float E1 = edge_bound(bx, by, cx, cy, mb, mc);
+  const float E2 = edge_bound(cx, cy, ax, ay, mc, ma);
   bool p0 = e0 > E0, p1 = e1 > E1, p2 = e2 > E2;
   bool n0 = e0 < -E0, n1 = e1 < -E1, n2 = e2 < -E2;
   if ((p0 || p1 || p2) && (n0 || n1 || n2)) return 0;
@@ -45,9 +67,12 @@ __device__ __forceinline__ int classify32(float ax, float ay, float bx, float by
     w[0] = e1 * inv;
     w[1] = e2 * inv;
     w[2] = e0 * inv;
-    float sE = E0 + E1 + E2;
-    // |dw_v| <= (E_v + w_v sE)/(|det| - sE); x = A + w_B (B-A) + w_C (C-A)
-    *pos_err = 1.1f * 2.0f * sE / (fabsf(det) - sE);
+    const float sE = __fadd_ru(__fadd_ru(__fadd_ru(E0, E1), E2),
+                               __fmul_ru(u2_up(), __fadd_ru(__fadd_ru(fabsf(e0), fabsf(e1)),
+                                                            fabsf(e2))));
+    const float den = __fsub_rd(fabsf(det), sE);
+    *pos_err = den > 0.0f ? __fadd_ru(__fdiv_ru(__fmul_ru(2.0f, sE), den), 4.8e-7f)
+                          : __int_as_float(0x7f800000);
     return 1;
   }
   return 2;
@@ -103,6 +128,10 @@ __device__ __forceinline__ float warp_max(float v) {
   asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
   return r;
 }
+
+// A vertex bound with its second-order terms: the first-order sum times
+// (1 + 8u), rounded up.
+__device__ __forceinline__ float mu_up(float m) { return __fmul_ru(m, 1.00000048f); }
 
 struct StripBox {
   float tx0, tx1, ty0, ty1, ax0, ax1, ay0, ay1, e, l;
@@ -277,7 +306,8 @@ __global__ void __launch_bounds__(kSearchThreads, 4)
         for (int v = threadIdx.x; v < sn; v += kSearchThreads) {
           const float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
           ss[v] = SrcSmem{px, py, (float)sr[s0 + v],
-                          u * (4.0f * g.theta_max + fabsf(px) + fabsf(py))};
+                          __fmul_ru(u, __fmaf_ru(4.0f, g.theta_max,
+                                                 __fadd_ru(fabsf(px), fabsf(py))))};
         }
       }
       staged = whole ? sample : -1;
@@ -288,10 +318,14 @@ __global__ void __launch_bounds__(kSearchThreads, 4)
         const int w = pidx % kStrips, k = pidx / kStrips;
         const StripBox B = sb[w];
         const SrcSmem S = ss[k];
-        const float wmu = fmaf(S.r, B.e, S.mu0 + u * (2.0f * (fabsf(B.tx0) + fabsf(B.tx1) +
-                                                              fabsf(B.ty0) + fabsf(B.ty1) +
-                                                              fabsf(S.px) + fabsf(S.py)) +
-                                                       4.0f * S.r * B.l));
+        const float wmu = mu_up(__fmaf_ru(
+            S.r, B.e,
+            __fmaf_ru(u, __fmaf_ru(2.0f,
+                                   __fadd_ru(__fadd_ru(__fadd_ru(fabsf(B.tx0), fabsf(B.tx1)),
+                                                       __fadd_ru(fabsf(B.ty0), fabsf(B.ty1))),
+                                             __fadd_ru(fabsf(S.px), fabsf(S.py))),
+                                   __fmul_ru(__fmul_ru(4.0f, S.r), B.l)),
+                      S.mu0)));
         const float bx0 = fmaf(-S.r, B.ax1, B.tx0), bx1 = fmaf(-S.r, B.ax0, B.tx1);
         const float by0 = fmaf(-S.r, B.ay1, B.ty0), by1 = fmaf(-S.r, B.ay0, B.ty1);
         const bool keep = B.any && S.px >= bx0 - wmu && S.px <= bx1 + wmu &&
@@ -314,9 +348,11 @@ __global__ void __launch_bounds__(kSearchThreads, 4)
         const float a02x = fmaf(-S.r, v02.x, dl), a02y = fmaf(-S.r, v02.y, dt);
         const float a12x = fmaf(-S.r, v12.x, dr), a12y = fmaf(-S.r, v12.y, dt);
         const float dxm = fmaxf(fabsf(dl), fabsf(dr));
-        const float base = S.mu0 + u * 2.0f * S.r * lmax;
-        const float muA = fmaf(S.r, emax, fmaf(u * 2.0f, dxm + fmaxf(fabsf(db), fabsf(dm)), base));
-        const float muB = fmaf(S.r, emax, fmaf(u * 2.0f, dxm + fmaxf(fabsf(dm), fabsf(dt)), base));
+        const float base = __fmaf_ru(__fmul_ru(u * 2.0f, S.r), lmax, S.mu0);
+        const float muA = mu_up(__fmaf_ru(
+            S.r, emax, __fmaf_ru(u * 2.0f, __fadd_ru(dxm, fmaxf(fabsf(db), fabsf(dm))), base)));
+        const float muB = mu_up(__fmaf_ru(
+            S.r, emax, __fmaf_ru(u * 2.0f, __fadd_ru(dxm, fmaxf(fabsf(dm), fabsf(dt))), base)));
         const bool candA = validA && fminf(fminf(a00x, a10x), fminf(a01x, a11x)) <= muA &&
                            fmaxf(fmaxf(a00x, a10x), fmaxf(a01x, a11x)) >= -muA &&
                            fminf(fminf(a00y, a10y), fminf(a01y, a11y)) <= muA &&
@@ -328,15 +364,17 @@ __global__ void __launch_bounds__(kSearchThreads, 4)
         if (!__any_sync(0xffffffffu, candA || candB)) continue;
         // per-vertex bounds
         auto muv = [&](const float4& v, float d) {
-          return fmaf(S.r, v.z, S.mu0 + u * (2.0f * d + 2.0f * S.r * (fabsf(v.x) + fabsf(v.y))));
+          return mu_up(__fmaf_ru(
+              S.r, v.z,
+              __fmaf_ru(u * 2.0f, __fmaf_ru(S.r, __fadd_ru(fabsf(v.x), fabsf(v.y)), d), S.mu0)));
         };
         int r0 = 0, r1 = 0;
         float w0[3], w1[3], pe0 = 0.0f, pe1 = 0.0f;
-        const float m01 = muv(v01, fabsf(dl) + fabsf(dm));
-        const float m11 = muv(v11, fabsf(dr) + fabsf(dm));
+        const float m01 = muv(v01, __fadd_ru(fabsf(dl), fabsf(dm)));
+        const float m11 = muv(v11, __fadd_ru(fabsf(dr), fabsf(dm)));
         if (candA) {
-          const float m00 = muv(v00, fabsf(dl) + fabsf(db));
-          const float m10 = muv(v10, fabsf(dr) + fabsf(db));
+          const float m00 = muv(v00, __fadd_ru(fabsf(dl), fabsf(db)));
+          const float m10 = muv(v10, __fadd_ru(fabsf(dr), fabsf(db)));
           // T0 = (v00, v10, v11), T1 = (v00, v11, v01)
           r0 = classify32(a00x, a00y, a10x, a10y, a11x, a11y, m00, m10, m11, w0, &pe0);
           r1 = classify32(a00x, a00y, a11x, a11y, a01x, a01y, m00, m11, m01, w1, &pe1);
@@ -353,8 +391,8 @@ __global__ void __launch_bounds__(kSearchThreads, 4)
         pe0 = 0.0f;
         pe1 = 0.0f;
         if (candB) {
-          const float m02 = muv(v02, fabsf(dl) + fabsf(dt));
-          const float m12 = muv(v12, fabsf(dr) + fabsf(dt));
+          const float m02 = muv(v02, __fadd_ru(fabsf(dl), fabsf(dt)));
+          const float m12 = muv(v12, __fadd_ru(fabsf(dr), fabsf(dt)));
           // the cell above: T0 = (v01, v11, v12), T1 = (v01, v12, v02)
           r0 = classify32(a01x, a01y, a11x, a11y, a12x, a12y, m01, m11, m12, w0, &pe0);
           r1 = classify32(a01x, a01y, a12x, a12y, a02x, a02y, m01, m12, m02, w1, &pe1);
