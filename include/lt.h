@@ -131,10 +131,14 @@ typedef struct {
 /* Counters of the last compute call, for reporting. */
 typedef struct {
   int64_t hits;          /* predicted images found (all samples) */
-  int64_t ambiguous;     /* (triangle, source) pairs sent to the FP64 predicate */
-  int64_t refined;       /* FP32 hits re-interpolated in FP64 */
-  int64_t fp64_nodes;    /* node deflections evaluated in FP64 by those */
+  int64_t ambiguous;     /* (triangle, source) pairs the search's coarse FP32
+                            bound left undecided */
+  int64_t refined;       /* certain FP32 hits whose position bound was too large */
+  int64_t fp64_nodes;    /* node deflections evaluated in FP64 */
   int64_t work_overflow; /* items dropped for lack of capacity (0 when OK) */
+  int64_t tight_nodes;   /* distinct nodes of those items re-evaluated in FP32
+                            with the tight bound */
+  int64_t fp64_items;    /* items the tight bound left undecided, decided in FP64 */
 } lt_stats;
 
 /* Create a model for `batch` samples of `n_pot` potentials.  Allocates the

@@ -80,7 +80,8 @@ struct lt_model {
   double* d_match_xy = nullptr;
   double* d_chi2_terms = nullptr;  // chi^2 term of each observed image [batch][n_obs]
   // FP64 resolution scratch (node table, vertex slots, distinct-node list)
-  ResolveScratch rs{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  ResolveScratch rs{nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                    nullptr, nullptr, nullptr, nullptr};
   size_t rs_vslot_alloc = 0;
   double2* d_adj_lam = nullptr;   // adjoint: lambda per matched observed image
   AdjPt* d_adj_pts = nullptr;   // adjoint points (x, y, coefficient) [batch][4 n_obs]
@@ -353,20 +354,29 @@ lt_status ensure_resolve(lt_model* m) {
   const size_t vslots = (size_t)max_nb * m->work_cap * 3;
   if (cap > m->rs.cap) {
     ++m->ws_epoch;
-    if (m->rs.keys) LT_CUDA(cudaFree(m->rs.keys));
-    if (m->rs.hval) LT_CUDA(cudaFree(m->rs.hval));
-    if (m->rs.ulist) LT_CUDA(cudaFree(m->rs.ulist));
+    void* old[] = {m->rs.keys, m->rs.hval, m->rs.ulist, m->rs.tval, m->rs.flag64, m->rs.ulist64};
+    for (void* q : old)
+      if (q) LT_CUDA(cudaFree(q));
     m->rs.keys = nullptr; m->rs.hval = nullptr; m->rs.ulist = nullptr; m->rs.cap = 0;
+    m->rs.tval = nullptr; m->rs.flag64 = nullptr; m->rs.ulist64 = nullptr;
     LT_CUDA(cudaMalloc(&m->rs.keys, sizeof(unsigned long long) * cap));
     LT_CUDA(cudaMalloc(&m->rs.hval, sizeof(double2) * cap));
     LT_CUDA(cudaMalloc(&m->rs.ulist, sizeof(int32_t) * cap));
-    // empty once here; every resolution leaves it empty again (k_res_tri)
+    LT_CUDA(cudaMalloc(&m->rs.tval, sizeof(float4) * cap));
+    LT_CUDA(cudaMalloc(&m->rs.flag64, sizeof(uint32_t) * cap));
+    LT_CUDA(cudaMalloc(&m->rs.ulist64, sizeof(int32_t) * cap));
+    // empty once here; every resolution leaves them empty again (k_res_tri)
     LT_CUDA(cudaMemset(m->rs.keys, 0xff, sizeof(unsigned long long) * cap));
+    LT_CUDA(cudaMemset(m->rs.flag64, 0, sizeof(uint32_t) * cap));
     m->rs.cap = cap;
   }
   if (!m->rs.n_unique) {
     LT_CUDA(cudaMalloc(&m->rs.n_unique, sizeof(unsigned int)));
     LT_CUDA(cudaMemset(m->rs.n_unique, 0, sizeof(unsigned int)));
+  }
+  if (!m->rs.n64) {
+    LT_CUDA(cudaMalloc(&m->rs.n64, sizeof(unsigned int)));
+    LT_CUDA(cudaMemset(m->rs.n64, 0, sizeof(unsigned int)));
   }
   if (vslots > m->rs_vslot_alloc) {
     ++m->ws_epoch;
@@ -425,8 +435,9 @@ lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int
     float4* nodes = (float4*)m->d_nodes;
     {
       ProfScope ps(m, st, 0, np, 0);
+      // the coarse bound: the resolution re-evaluates undecided nodes tightly
       LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)c.b0 * m->n_pot, m->d_seg + c.b0, m->n_pot,
-                               g, di, nb, c.defl_items, m->shape, nodes, next_defl,
+                               g, di, nb, c.defl_items, m->shape, false, nodes, next_defl,
                                m->sm_count, st));
     }
     if (wait_before_search) LT_CUDA(cudaStreamWaitEvent(st, wait_before_search, 0));
@@ -436,13 +447,19 @@ lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int
                               m->work_cap, hc, wc, m->d_counters, m->d_status, next_search,
                               m->sm_count, st));
     }
-    ProfScope ps(m, st, 2, 0.0, 0, 3);  // k_res_insert, k_res_nodes, k_res_tri
+    // k_res_insert, k_res_tight32, k_res_tri32, k_res_nodes, k_res_tri
+    ProfScope ps(m, st, 2, 0.0, 0, 5);
     const cudaError_t re =
-        launch_resolve64(m->d_pot64, m->n_pot, g, src, work, wc, nb, m->work_cap, hits, hit_cap,
-                         hc, m->d_counters, m->d_status, m->rs, m->sm_count, st);
+        launch_resolve64(m->d_pot64, m->d_pot32 + (size_t)c.b0 * m->n_pot, m->d_seg + c.b0,
+                         m->n_pot, g, src, work, wc, nb, m->work_cap, hits, hit_cap, hc,
+                         m->d_counters, m->d_status, m->rs, m->sm_count, st);
     // a failed launch may leave the table partly filled: reallocate (and so
     // clear) it on the next call
-    if (re != cudaSuccess) m->rs.cap = 0;
+    if (re != cudaSuccess) {
+      m->rs.cap = 0;
+      if (m->rs.n_unique) cudaMemsetAsync(m->rs.n_unique, 0, sizeof(unsigned int), st);
+      if (m->rs.n64) cudaMemsetAsync(m->rs.n64, 0, sizeof(unsigned int), st);
+    }
     LT_CUDA(re);
   }
   return LT_OK;
@@ -584,7 +601,8 @@ void lt_model_destroy(lt_model* m) {
                   m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched,
                   m->d_src_beta, m->d_src_mu, m->d_src_bary, m->d_chi2_terms, m->rs.keys,
                   m->rs.hval,
-                  m->rs.vslot, m->rs.ulist, m->rs.n_unique};
+                  m->rs.vslot, m->rs.ulist, m->rs.n_unique, m->rs.tval, m->rs.flag64,
+                  m->rs.ulist64, m->rs.n64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -669,8 +687,11 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
     if (s2 != LT_OK) return s2;
   }
   LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long), st));
+  // the tight bound where the caller asks for it, the cheaper coarse kernel
+  // otherwise (its bound is not output; the deflection is the same)
+  const bool tight = err_out != nullptr && precision == LT_PREC_MIXED;
   LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)sample * m->n_pot, m->d_seg + sample, m->n_pot,
-                           &dev->g, dev->items, 1, items[1], m->shape, nodes4, m->d_sched,
+                           &dev->g, dev->items, 1, items[1], m->shape, tight, nodes4, m->d_sched,
                            m->sm_count, st));
   if (precision == LT_PREC_MIXED) {
     LT_CUDA(launch_unpack32(nodes4, nodes, (float2*)alpha_out, err_out, st));
@@ -874,6 +895,8 @@ lt_status lt_model_sync(lt_model* m, uintptr_t stream, lt_stats* stats) {
     stats->refined = cnt[CNT_REFINE];
     stats->fp64_nodes = cnt[CNT_FP64_NODES];
     stats->work_overflow = cnt[CNT_DROPPED];
+    stats->tight_nodes = cnt[CNT_TIGHT_NODES];
+    stats->fp64_items = cnt[CNT_FP64_ITEMS];
   }
   if (status & ST_NONFINITE) {
     m->err = "non-finite or out-of-domain lens parameter";
@@ -971,7 +994,8 @@ lt_status lt_autotune(lt_model* m, const lt_grid* grid, uintptr_t stream, int32_
       LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long), st));
       LT_CUDA(cudaEventRecord(e0, st));
       LT_CUDA(launch_deflect32(m->d_pot32, m->d_seg, m->n_pot, &dplan[v].g, dplan[v].items, 1,
-                               hs[v].items[1], v, (float4*)base, m->d_sched, m->sm_count, st));
+                               hs[v].items[1], v, false, (float4*)base, m->d_sched, m->sm_count,
+                               st));
       LT_CUDA(cudaEventRecord(e1, st));
       LT_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;

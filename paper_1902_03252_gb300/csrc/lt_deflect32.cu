@@ -13,7 +13,10 @@ namespace lt {
 // --------------------------------------------------------------- deflection
 // MINB: the resident blocks per SM the register allocation must allow (left
 // to the compiler, the (256, 4) shape is squeezed into 64 registers and spills)
-template <int NT, int NPT, int MINB>
+// TIGHT: the node's tight running bound (deflection grids with a bound) or
+// the coarse one (the chi^2 path, whose undecided triangles are re-evaluated
+// with the tight bound); see lt_fp32.cuh.
+template <int NT, int NPT, int MINB, bool TIGHT>
 __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict__ pot32,
                                                   const Seg32* __restrict__ seg, int n_pot,
                                                   const SampleGrid* __restrict__ grids,
@@ -49,66 +52,70 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
     float Y[NPT], AX[NPT], AY[NPT], ER[NPT];
 #pragma unroll
     for (int m = 0; m < NPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
-    deflect32_nodes<NT, NPT>(pot32 + (int64_t)b * n_pot, n_pot, sg, g.theta_max, X, Y, sp, AX,
-                             AY, ER);
-    const float qs = sg.q_tot;
+    deflect32_nodes<NT, NPT, TIGHT>(pot32 + (int64_t)b * n_pot, n_pot, sg, g.theta_max, X, Y,
+                                    sp, AX, AY, ER);
+    const float qs = TIGHT ? sg.q_tot : sg.c_tot;
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
       if (live && j0 + m < g.ny)
         node_out[g.node_off + (int64_t)(j0 + m) * g.nx + i] =
-            make_float4(AX[m], AY[m], node_bound(__fadd_ru(ER[m], qs)), 0.0f);
+            make_float4(AX[m], AY[m], node_bound(__fadd_ru(ER[m], qs), n_pot), 0.0f);
     }
   }
 }
 
-template <int NT, int NPT, int MINB>
+template <int NT, int NPT, int MINB, bool TIGHT>
 static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int n_pot,
                                       const SampleGrid* grids, const int64_t* item_off,
                                       int n_samples, int64_t n_items, float4* node_out,
                                       unsigned long long* next_item, int sm_count,
                                       cudaStream_t st) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32<NT, NPT, MINB>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32<NT, NPT, MINB, TIGHT>, NT,
+                                                0);
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)sm_count * per_sm;
   if (blocks > n_items) blocks = n_items;
   if (blocks < 1) return cudaSuccess;
-  return launch_pdl(k_deflect32<NT, NPT, MINB>, dim3((unsigned)blocks), dim3(NT), st, pot32, seg,
-                    n_pot, grids, item_off, n_samples, n_items, node_out, next_item);
+  return launch_pdl(k_deflect32<NT, NPT, MINB, TIGHT>, dim3((unsigned)blocks), dim3(NT), st,
+                    pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item);
 }
 
 template <int V>
 static cudaError_t launch_shape(const Pot32* pot32, const Seg32* seg, int n_pot,
                                const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                               int64_t n_items, float4* node_out, unsigned long long* next_item,
-                               int sm_count, cudaStream_t st) {
+                               int64_t n_items, bool tight, float4* node_out,
+                               unsigned long long* next_item, int sm_count, cudaStream_t st) {
   constexpr DeflectShape sh = deflect_shape(V);
-  return launch_deflect32_t<sh.threads, sh.npt, sh.min_blocks>(
+  if (tight)
+    return launch_deflect32_t<sh.threads, sh.npt, sh.min_blocks, true>(
+        pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item, sm_count, st);
+  return launch_deflect32_t<sh.threads, sh.npt, sh.min_blocks, false>(
       pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item, sm_count, st);
 }
 
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
                              const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, float4* node_out,
+                             int64_t n_items, int shape, bool tight, float4* node_out,
                              unsigned long long* next_item, int sm_count, cudaStream_t st) {
   static_assert(kNumShapes == 8, "one case per launch shape");
   switch (shape) {
     case 1: return launch_shape<1>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     case 2: return launch_shape<2>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     case 3: return launch_shape<3>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     case 4: return launch_shape<4>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     case 5: return launch_shape<5>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     case 6: return launch_shape<6>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     case 7: return launch_shape<7>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   node_out, next_item, sm_count, st);
+                                   tight, node_out, next_item, sm_count, st);
     default: return launch_shape<0>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                    node_out, next_item, sm_count, st);
+                                    tight, node_out, next_item, sm_count, st);
   }
 }
 

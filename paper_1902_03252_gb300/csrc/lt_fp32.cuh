@@ -22,12 +22,27 @@ namespace lt {
 // by the total once per group, instead of every term by the running total:
 // with n potentials the running-sum part of the bound shrinks from about
 // n |alpha| to about (kSumGroup + n / kSumGroup) |alpha|, and so does the
-// error itself.
-constexpr int kSumGroup = 32;
+// error itself.  (kSumGroup and the staging chunk kChunk32 are defined with
+// the records in lt_internal.cuh: k_prep derives the coarse bound from them.)
 
-// The bound's terms are accumulated with upward rounding (__fmaf_ru,
-// __fadd_ru), so that the float sums never fall below the exact sums of the
-// terms; the terms themselves are derived in k_prep.
+// The bound's terms are non-negative and are accumulated with round-to-
+// nearest FMAs (directed rounding measured slower on the FMA pipes): a float
+// sum of non-negative terms through k roundings is at least the exact sum
+// times 1 - gamma(k), which node_bound covers with its factor
+// 1 + (6 n_pot + 64) u (at most five roundings per potential, two per
+// group); the terms themselves are derived in k_prep.
+//
+// Two forms of the bound (template flag TIGHT):
+//  * tight: per node and potential the term P / d, the evaluation terms
+//    Gx |gx| + Gy |gy| of the PIEMD and the accumulation terms 2 (|PX| + |PY|)
+//    per step and 2 (|AX| + |AY|) per group;
+//  * coarse: only P / d per node and potential; the evaluation and
+//    accumulation terms are replaced by their largest values over the plane,
+//    summed once per sample in k_prep (Seg32::c_tot).  Valid everywhere and
+//    about twice the tight bound on cluster lenses; four instructions per
+//    node and potential cheaper.  The triangle search certifies what it can
+//    with the coarse bound, and the resolution re-evaluates the few
+//    undecided nodes with the tight one (k_res_tight32).
 
 // Coefficient P of the per-node term P / d of one potential (units of u) on a
 // grid whose largest |node coordinate| is theta1: errP0 W, W = theta1 + |cx| +
@@ -49,14 +64,14 @@ __device__ __forceinline__ float stage_p32(const Pot32& r, bool piemd, float the
 
 // Add a group's partial sums to the totals (one rounding per component,
 // bounded by the new total) and clear them.
-template <int NPT>
+template <int NPT, bool TIGHT>
 __device__ __forceinline__ void flush_group(float* AX, float* AY, float* PX, float* PY,
                                             float* ER) {
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     AX[m] += PX[m];
     AY[m] += PY[m];
-    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
+    if (TIGHT) ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
     PX[m] = 0.0f;
     PY[m] = 0.0f;
   }
@@ -65,7 +80,7 @@ __device__ __forceinline__ void flush_group(float* AX, float* AY, float* PX, flo
 // One SIS: alpha += b0 (theta - c)/R (zero at the centre).  err accumulates in
 // units of the FP32 unit roundoff.  In this and the two functions below, AX
 // and AY are a group's partial sums (flush_group).
-template <int NPT>
+template <int NPT, bool TIGHT>
 __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, const float* Y,
                                             float* AX, float* AY, float* ER) {
   const float dx = X - f[0].x;
@@ -81,8 +96,8 @@ __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, c
     const float g = f[0].z * ri;
     AX[m] = fmaf(g, dx, AX[m]);
     AY[m] = fmaf(g, dy, AY[m]);
-    ER[m] = __fmaf_ru(P, rr, ER[m]);
-    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
+    ER[m] = fmaf(P, rr, ER[m]);
+    if (TIGHT) ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
   }
 }
 
@@ -96,7 +111,7 @@ __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, c
 // f[0] = {cx, cy, sqrt(1-eps) c, sqrt(1-eps) s},
 // f[1] = {sqrt(1+eps) c, sqrt(1+eps) s, b0 sqrt(1-eps) c, b0 sqrt(1+eps) s},
 // f[2] = {b0 sqrt(1+eps) c, b0 sqrt(1-eps) s, 0, 0}.
-template <int NPT>
+template <int NPT, bool TIGHT>
 __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, const float* Y,
                                             float* AX, float* AY, float* ER) {
   const float dx = X - f[0].x;
@@ -113,8 +128,8 @@ __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, c
     const float t2 = fmaf(f[2].x, v, f[2].y * u);
     AX[m] = fmaf(ri, t1, AX[m]);
     AY[m] = fmaf(ri, t2, AY[m]);
-    ER[m] = __fmaf_ru(P, rr, ER[m]);
-    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
+    ER[m] = fmaf(P, rr, ER[m]);
+    if (TIGHT) ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
   }
 }
 
@@ -136,7 +151,7 @@ __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, c
 // lenses) are then recomputed by those functions.  Every node gets exactly
 // the values and roundings of the per-node evaluation; the merged test
 // removes most of the branch instructions from the issue stream.
-template <int NPT>
+template <int NPT, bool TIGHT>
 __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X, const float* Y,
                                               float* AX, float* AY, float* ER) {
   const float cy = f[0].y, c = f[0].z, s = f[0].w;
@@ -196,14 +211,13 @@ __device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X,
     const float gy = ty[m] * py_[m];
     AX[m] = fmaf(gx, Bc, fmaf(-gy, Bs, AX[m]));
     AY[m] = fmaf(gy, Bc, fmaf(gx, Bs, AY[m]));
-    ER[m] = __fmaf_ru(P, ra[m], ER[m]);
-    ER[m] = __fmaf_ru(f[4].y, fabsf(gx), __fmaf_ru(f[4].z, fabsf(gy), ER[m]));
-    ER[m] = __fmaf_ru(2.0f, __fadd_ru(fabsf(AX[m]), fabsf(AY[m])), ER[m]);
+    ER[m] = fmaf(P, ra[m], ER[m]);
+    if (TIGHT) {
+      ER[m] = fmaf(f[4].y, fabsf(gx), fmaf(f[4].z, fabsf(gy), ER[m]));
+      ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    }
   }
 }
-
-// Potentials staged in shared memory at a time by the deflection kernels.
-constexpr int kChunk32 = 256;
 
 // Stage potentials [c0, c0 + cn) of a sample's records into shared memory,
 // f[4].x replaced by the grid's coefficient P (stage_p32).  Called by all NT
@@ -223,13 +237,13 @@ __device__ __forceinline__ void stage_chunk32(float4* sp, const Pot32* __restric
 }
 
 // The per-item body of both FP32 deflection kernels: the deflection (AX, AY)
-// and the running-bound terms ER of one thread's NPT nodes (column X, rows
+// and the running-bound terms ER (tight or coarse) of one thread's NPT nodes (column X, rows
 // Y[]) over all n_pot potentials of one sample, kind segment by kind segment
 // ([0, n_sis) SIS, then PIEMD, then SIE), in groups of at most kSumGroup
 // potentials whose partial sums join the totals once per group.  The order of
 // every operation of a node depends only on the potentials, not on NT or NPT.
 // sp: shared memory of kChunk32 * 5 float4; called by all NT threads.
-template <int NT, int NPT>
+template <int NT, int NPT, bool TIGHT>
 __device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, int n_pot,
                                                 const Seg32& sg, float theta1, float X,
                                                 const float* Y, float4* sp, float* AX,
@@ -252,18 +266,18 @@ __device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, in
     const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
     for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
       for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k)
-        sis32_nodes<NPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-      flush_group<NPT>(AX, AY, PX, PY, ER);
+        sis32_nodes<NPT, TIGHT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+      flush_group<NPT, TIGHT>(AX, AY, PX, PY, ER);
     }
     for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
       for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k)
-        piemd32_nodes<NPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-      flush_group<NPT>(AX, AY, PX, PY, ER);
+        piemd32_nodes<NPT, TIGHT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+      flush_group<NPT, TIGHT>(AX, AY, PX, PY, ER);
     }
     for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
       for (int k = k0; k < min(k0 + kSumGroup, cn); ++k)
-        sie32_nodes<NPT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-      flush_group<NPT>(AX, AY, PX, PY, ER);
+        sie32_nodes<NPT, TIGHT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
+      flush_group<NPT, TIGHT>(AX, AY, PX, PY, ER);
     }
   }
 }

@@ -43,6 +43,32 @@ __device__ __forceinline__ bool valid_params(const double* v, int* kind_out) {
   return ok;
 }
 
+// Summation weights of the potential at kind-sorted position r, for the
+// chunk / kind-segment / group order of the FP32 deflection: *w_partial the
+// accumulation steps whose partial sum contains its term (its own and the
+// later steps of its group), *w_flush the group flushes whose total contains
+// it (its group's and every later one).
+__device__ void sum_weights(int r, int n_pot, int n_sis, int n_piemd, int* w_partial,
+                            int* w_flush) {
+  int groups = 0, mine = 0;
+  *w_partial = 1;
+  for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
+    const int cn = min(kChunk32, n_pot - c0);
+    const int seg[4] = {0, min(max(n_sis - c0, 0), cn), min(max(n_sis + n_piemd - c0, 0), cn),
+                        cn};
+    for (int t = 0; t < 3; ++t)
+      for (int k0 = seg[t]; k0 < seg[t + 1]; k0 += kSumGroup) {
+        const int k1 = min(k0 + kSumGroup, seg[t + 1]);
+        if (r >= c0 + k0 && r < c0 + k1) {
+          mine = groups;
+          *w_partial = c0 + k1 - r;
+        }
+        ++groups;
+      }
+  }
+  *w_flush = groups - mine;
+}
+
 // One block per sample.  Pass 1 validates every potential and writes its
 // FP64 record (invalid ones are latched and neutralised to a zero-mass SIS);
 // pass 2 ranks potentials kind-major in index order (block-wide ballot
@@ -58,7 +84,7 @@ __global__ void __launch_bounds__(kPrepThreads)
   Pot64* p64 = pot64 + (int64_t)b * n_pot;
   __shared__ int cnt[3];
   __shared__ int wcnt[3][NW];
-  __shared__ float qpart[NW];
+  __shared__ float qpart[NW], cpart[NW];
   if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < n_pot; k += kPrepThreads) {
@@ -89,7 +115,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     atomicAdd(&cnt[kind], 1);
   }
   __syncthreads();
-  float qsum = 0.0f;
+  float qsum = 0.0f, csum = 0.0f;
   int base[3] = {0, 0, 0};  // potentials of each kind in earlier chunks
   for (int k0 = 0; k0 < n_pot; k0 += kPrepThreads) {
     const int k = k0 + threadIdx.x;
@@ -148,7 +174,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     //    (Higham, Accuracy and Stability of Numerical Algorithms, Lemma 3.1).
     const double U = kU32d;
     auto gam = [U](double n) { return n * U >= 0.25 ? 1e30 : n / (1.0 - n * U); };
-    double Q;
+    double Q, T, Gmax = 0.0;
     if (kind == LT_SIS) {
       // Jacobian of b0 n(Delta): b0/|Delta| (2-norm).  Where |D| >= 2|e|:
       // error <= 2 b0 |e| / |D| with |e| <= u(1+u)(W2 + |Delta|), W2 =
@@ -162,6 +188,8 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[0] = make_float4(cx, cy, (float)p.b0, 0.f);
       f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
       Q = p.b0 * (gam(3.0 + kEpsRsqrt) + 3.0 * (1.0 + 3.0 * U));
+      // |t_x| + |t_y| = g (|dx| + |dy|) <= sqrt(2) b0 (1 + (3 + eps_r) u)
+      T = 1.41421357 * p.b0 * (1.0 + gam(5.0 + kEpsRsqrt) * U);
     } else if (kind == LT_SIE) {
       const double r1 = sqrt(1.0 - p.e), r2 = sqrt(1.0 + p.e);
       // z = (r1 x', r2 y'), g = b0 diag(r1, r2) z / |z|: Jacobian in z at most
@@ -183,6 +211,8 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[2] = make_float4((float)(p.b0 * r2 * p.c), (float)(p.b0 * r1 * p.s), 0.f, 0.f);
       f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
       Q = p.b0 * r2 * (gam(5.25 + kEpsRsqrt) + 16.04 * (1.0 + 3.0 * U) / r1);
+      // |t_x| + |t_y| <= sqrt(2) |rr (t1, t2)| <= sqrt(2) b0 r2 (1 + (6.25 + eps_r) u)
+      T = 1.41421357 * p.b0 * r2 * (1.0 + gam(6.25 + kEpsRsqrt) * U);
     } else {
       const double a = p.a, sc = p.sc, q2 = p.q2, q = p.q;
       const double B = p.scale;
@@ -241,19 +271,43 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[4] = make_float4(__double2float_ru(p0), __double2float_ru(Gx * Bs),
                            __double2float_ru(Gy * Bs), (float)(Bs * p.s));
       Q = 16.04 * (1.0 + 3.0 * U) * B / q;
+      // coarse bound: the largest |gx|, |gy| over the plane.  |g_x| =
+      // |atan(A) - atan(B)| <= atan(sig/q) (0 <= B <= A < sig/q) and |g_y| <=
+      // atanh(sig) (the two atanh arguments lie in (-sig, sig) with one sign),
+      // each times its evaluation factor 1 + G u.
+      const double mgx = atan(sig / q) * (1.0 + Gx * U);
+      const double mgy = atanh(fmin(sig, 1.0 - 1e-16)) * (1.0 + Gy * U);
+      Gmax = Bs * (Gx * mgx + Gy * mgy);
+      // |t_x| + |t_y| <= (B/sig)(|c| + |s|)(|gx| + |gy|)(1 + u)
+      T = Bs * (fabs(p.c) + fabs(p.s)) * (mgx + mgy) * (1.0 + 2.0 * U);
     }
     qsum = __fadd_ru(qsum, __double2float_ru(Q));
+    // coarse bound: Q, the largest evaluation terms, and every accumulation
+    // step's 2 (|PX| + |PY|) and flush's 2 (|AX| + |AY|) bounded by the
+    // largest terms they can contain
+    int w_partial, w_flush;
+    sum_weights(rank, n_pot, cnt[LT_SIS], cnt[LT_PIEMD], &w_partial, &w_flush);
+    csum = __fadd_ru(csum, __double2float_ru(Q + Gmax + 2.0 * T * (w_partial + w_flush)));
     pot32[(int64_t)b * n_pot + rank] = f;
   }
   // sum of the static bound terms (rounded up): fixed order (warp
   // butterflies, then warps)
-  for (int o = 16; o > 0; o >>= 1) qsum = __fadd_ru(qsum, __shfl_xor_sync(0xffffffffu, qsum, o));
-  if (lane == 0) qpart[wid] = qsum;
+  for (int o = 16; o > 0; o >>= 1) {
+    qsum = __fadd_ru(qsum, __shfl_xor_sync(0xffffffffu, qsum, o));
+    csum = __fadd_ru(csum, __shfl_xor_sync(0xffffffffu, csum, o));
+  }
+  if (lane == 0) {
+    qpart[wid] = qsum;
+    cpart[wid] = csum;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float tot = 0.0f;
-    for (int w = 0; w < NW; ++w) tot += qpart[w];
-    seg[b] = Seg32{cnt[LT_SIS], cnt[LT_PIEMD], cnt[LT_SIE], tot};
+    float tot = 0.0f, ctot = 0.0f;
+    for (int w = 0; w < NW; ++w) {
+      tot = __fadd_ru(tot, qpart[w]);
+      ctot = __fadd_ru(ctot, cpart[w]);
+    }
+    seg[b] = Seg32{cnt[LT_SIS], cnt[LT_PIEMD], cnt[LT_SIE], tot, ctot};
   }
 }
 
@@ -504,10 +558,13 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
 //                 capacity >= twice the number of vertices, so it cannot
 //                 fill); the thread that inserts a key appends its slot to
 //                 the list of distinct nodes;
-//   k_res_nodes   one block per distinct node: FP64 deflection summed in
-//                 potential index order (block_alpha64);
-//   k_res_tri     one thread per item: exact FP64 predicates with the tie
-//                 rule and the FP64 barycentric position.
+//   (the tight FP32 stage, launch_tight32: each distinct node re-evaluated
+//                 with its tight bound and every item classified again; the
+//                 items it decides are done)
+//   k_res_nodes   one block per node of an item still undecided: FP64
+//                 deflection summed in potential index order (block_alpha64);
+//   k_res_tri     one thread per item still undecided: exact FP64 predicates
+//                 with the tie rule and the FP64 barycentric position.
 constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr int kResNodeThreads = 128;
 
@@ -574,6 +631,8 @@ __global__ void __launch_bounds__(kResNodeThreads)
                 const SampleGrid* __restrict__ grids, const unsigned long long* __restrict__ keys,
                 const int32_t* __restrict__ ulist, const unsigned int* __restrict__ n_unique,
                 double2* __restrict__ hval, long long* counters) {
+  // ulist / n_unique: the FP64 stage's list (nodes of the items the tight
+  // FP32 stage left undecided)
   grid_dependency_wait();
   __shared__ double2 buf[kResNodeThreads];
   __shared__ double res[2];
@@ -602,11 +661,15 @@ __global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
                           const double2* __restrict__ hval, Hit* __restrict__ hits,
                           int64_t hit_cap, unsigned long long* hit_count, long long* counters,
                           uint32_t* status, unsigned long long* __restrict__ keys,
-                          unsigned int* __restrict__ n_unique) {
+                          unsigned int* __restrict__ n_unique, uint32_t* __restrict__ flag64,
+                          unsigned int* __restrict__ n64) {
   grid_dependency_wait();
   // this kernel is the table's last reader: it leaves the table empty for the
-  // next call (the distinct-node list count here, every used slot below)
-  if (blockIdx.x == 0 && threadIdx.x == 0) *n_unique = 0u;
+  // next call (the list counts here, every used slot and its flag below)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *n_unique = 0u;
+    *n64 = 0u;
+  }
   long long n_hit = 0;
   const int64_t total = (int64_t)n_samples * work_cap;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total;
@@ -619,8 +682,12 @@ __global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
     // several items may share a slot: they all write the same value
     for (int v = 0; v < 3; ++v) {
       const int32_t slot = vslot[f * 3 + v];
-      if (slot >= 0) keys[slot] = kEmptyKey;
+      if (slot >= 0) {
+        keys[slot] = kEmptyKey;
+        flag64[slot] = 0u;
+      }
     }
+    if (wk.resolved) continue;  // decided by the tight FP32 stage
     const SampleGrid g = grids[b];
     const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
     const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
@@ -660,9 +727,10 @@ __global__ void k_res_tri(const SampleGrid* __restrict__ grids, Sources src,
     atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
 }
 
-cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* grids, Sources src,
-                             const Work64* work, const unsigned long long* work_count,
-                             int n_samples, int64_t work_cap, Hit* hits, int64_t hit_cap,
+cudaError_t launch_resolve64(const Pot64* pot64, const Pot32* pot32, const Seg32* seg, int n_pot,
+                             const SampleGrid* grids, Sources src, Work64* work,
+                             const unsigned long long* work_count, int n_samples,
+                             int64_t work_cap, Hit* hits, int64_t hit_cap,
                              unsigned long long* hit_count, long long* counters,
                              uint32_t* status, ResolveScratch rs, int sm_count,
                              cudaStream_t st) {
@@ -679,14 +747,17 @@ cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* gr
                              n_samples, work_cap, grids, rs.keys, cap - 1, rs.vslot, rs.ulist,
                              rs.n_unique);
   if (e != cudaSuccess) return e;
+  e = launch_tight32(pot32, seg, n_pot, grids, src, work, work_count, n_samples, work_cap, hits,
+                     hit_cap, hit_count, counters, status, rs, sm_count, st);
+  if (e != cudaSuccess) return e;
   e = launch_pdl(k_res_nodes, dim3(sm_count * 8), dim3(kResNodeThreads), st, pot64, n_pot,
-                 src.sample_base, grids, rs.keys, rs.ulist, rs.n_unique, rs.hval, counters);
+                 src.sample_base, grids, rs.keys, rs.ulist64, rs.n64, rs.hval, counters);
   if (e != cudaSuccess) return e;
   int64_t b3 = ((int64_t)n_samples * work_cap + 127) / 128;
   if (b3 > (int64_t)sm_count * 16) b3 = (int64_t)sm_count * 16;
-  return launch_pdl(k_res_tri, dim3((unsigned)b3), dim3(128), st, grids, src, work, work_count,
-                    n_samples, work_cap, rs.vslot, rs.hval, hits, hit_cap, hit_count, counters,
-                    status, rs.keys, rs.n_unique);
+  return launch_pdl(k_res_tri, dim3((unsigned)b3), dim3(128), st, grids, src,
+                    (const Work64*)work, work_count, n_samples, work_cap, rs.vslot, rs.hval, hits,
+                    hit_cap, hit_count, counters, status, rs.keys, rs.n_unique, rs.flag64, rs.n64);
 }
 
 // -------------------------------------------------------------- barycentres

@@ -19,7 +19,16 @@ enum : uint32_t {
 };
 
 // Counters written by kernels (int64, device), one set per model.
-enum { CNT_HITS = 0, CNT_AMBIG, CNT_REFINE, CNT_FP64_NODES, CNT_DROPPED, CNT_N };
+enum {
+  CNT_HITS = 0,
+  CNT_AMBIG,        // (triangle, source) pairs the coarse FP32 bound left undecided
+  CNT_REFINE,       // coarse-certain hits whose position bound was too large
+  CNT_FP64_NODES,   // distinct nodes evaluated in FP64
+  CNT_DROPPED,
+  CNT_TIGHT_NODES,  // distinct nodes re-evaluated with the tight FP32 bound
+  CNT_FP64_ITEMS,   // work items the tight bound left to FP64
+  CNT_N
+};
 
 constexpr double kC = 299792.458;         // km/s
 constexpr double kArcsec = 206264.80625;  // arcsec per radian
@@ -76,22 +85,35 @@ constexpr double kEpsAtanhc = 7.7;      // atanhc_sq32 on [0, 1/4] (7.574)
 constexpr double kEpsAtanhcLog = 5.0;   // (1 - u) x atanhc_sq32 on [1/4, 0.99999988] (4.917)
 constexpr double kU32d = 5.9604644775390625e-8;  // u as a double
 
-// A node's bound from its accumulated terms (units of u, accumulated with
-// upward rounding).  The factor 1 + 2^-16 covers the terms of second order
-// in u that the coefficients leave out (the FP64 rounding of the record
-// constants, the 2 + u of a fused accumulation step).  Capped at 1e30: a node
-// on an SIS/SIE centre has an infinite term, and a finite cap keeps every
-// later product (r E with r = 0 included) a number.
-__device__ __forceinline__ float node_bound(float terms) {
-  return fminf(__fmul_ru(__fmul_ru(kU32, 1.0000152587890625f), terms), 1e30f);
+// A node's bound from its accumulated terms (units of u) for a sample of
+// n_pot potentials.  The factor 1 + (6 n_pot + 64) u + 2^-16 covers the
+// round-to-nearest accumulation of the non-negative terms (at most five
+// roundings per potential and two per group, so a relative shortfall below
+// gamma(6 n_pot + 64)) and the terms of second order in u that the
+// coefficients leave out (the FP64 rounding of the record constants, the
+// 2 + u of a fused accumulation step).  Capped at 1e30: a node on an SIS/SIE
+// centre has an infinite term, and a finite cap keeps every later product
+// (r E with r = 0 included) a number.
+__device__ __forceinline__ float node_bound(float terms, int n_pot) {
+  const float f = __fmaf_ru((float)(6 * n_pot + 64), kU32, 1.0000152587890625f);
+  return fminf(__fmul_ru(__fmul_ru(kU32, f), terms), 1e30f);
 }
 
-// Per-sample kind segments of the FP32 records: [n_sis, n_piemd, n_sie, 0]
-// and the static part of the error bound, sum_k errQ_k (float).
+// Per-sample kind segments of the FP32 records (n_sis, n_piemd, n_sie), the
+// static part of the tight error bound, sum_k errQ_k, and the static part of
+// the coarse one, which adds every potential's largest evaluation and
+// accumulation terms (units of u, rounded up).
 struct Seg32 {
   int n_sis, n_piemd, n_sie;
-  float q_tot;
+  float q_tot, c_tot;
 };
+
+// Summation structure of the FP32 deflection: potentials are staged kChunk32
+// at a time (kind-sorted order), and within a chunk each kind segment is
+// summed in groups of at most kSumGroup potentials whose partial sums join
+// the node's total once per group.
+constexpr int kChunk32 = 256;
+constexpr int kSumGroup = 32;
 
 // ---------------------------------------------------- FP64 deflection (one)
 // atan(t)/t and atanh(t)/t as functions of t2 = t*t, with the short Taylor
@@ -336,8 +358,8 @@ struct SampleGrid {
 struct Work64 {
   int32_t sample, src;
   int64_t tri;
-  int32_t type;  // 0 = ambiguous pair, 1 = refine a certain hit
-  int32_t pad;
+  int32_t type;      // 0 = ambiguous pair, 1 = refine a certain hit
+  int32_t resolved;  // set by the tight FP32 stage when it decided the item
 };
 
 // Adjoint point: position and the 2-vector coefficient of d alpha there.
@@ -403,10 +425,11 @@ cudaError_t launch_zero64(unsigned long long* a, int64_t na, unsigned long long*
                           cudaStream_t st);
 cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64, Pot32* pot32,
                         Seg32* seg, uint32_t* status, cudaStream_t st);
-// next_item: a zeroed device counter, taken by atomicAdd (dynamic items)
+// next_item: a zeroed device counter, taken by atomicAdd (dynamic items);
+// tight: the node bound in its tight form (else the coarse one)
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
                              const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, float4* node_out,
+                             int64_t n_items, int shape, bool tight, float4* node_out,
                              unsigned long long* next_item, int sm_count, cudaStream_t st);
 cudaError_t launch_deflect64(const Pot64* pot64, int n_pot, const SampleGrid* grids,
                              const int64_t* item_off, int n_samples, int64_t n_items,
@@ -434,10 +457,12 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
                             int n_samples, int64_t n_items, Sources src, Hit* hits,
                             int64_t hit_cap, unsigned long long* hit_count, long long* counters,
                             uint32_t* status, int sm_count, cudaStream_t st);
-// Scratch of the FP64 resolution: node table (keys, values), per-vertex slots,
-// list of distinct nodes and its length.  cap: table entries (power of two)
-// allocated, at least the smallest power of two >= 6 x samples x work_cap of
-// any chunk.
+// Scratch of the resolution of undecided work items: node table (keys, FP64
+// values, tight FP32 values), per-vertex slots, list of distinct nodes and
+// its length, and the FP64 stage's node flags and list.  cap: table entries
+// (power of two) allocated, at least the smallest power of two >= 6 x
+// samples x work_cap of any chunk.  Every resolution leaves keys, flag64,
+// n_unique and n64 as it found them (all empty).
 struct ResolveScratch {
   unsigned long long* keys;
   double2* hval;
@@ -445,13 +470,30 @@ struct ResolveScratch {
   int32_t* ulist;  // [cap]
   unsigned int* n_unique;
   unsigned long long cap;
+  float4* tval;      // [cap] tight FP32 (alpha_x, alpha_y, bound, 0) per slot
+  uint32_t* flag64;  // [cap] 1 once a slot is listed for FP64
+  int32_t* ulist64;  // [cap] slots to evaluate in FP64
+  unsigned int* n64;
 };
-cudaError_t launch_resolve64(const Pot64* pot64, int n_pot, const SampleGrid* grids, Sources src,
-                             const Work64* work, const unsigned long long* work_count,
-                             int n_samples, int64_t work_cap, Hit* hits, int64_t hit_cap,
+// Resolution of a chunk's undecided work items: distinct nodes keyed
+// (k_res_insert), re-evaluated in FP32 with the tight bound and the items
+// re-classified (launch_tight32), the nodes of the items still undecided
+// evaluated in FP64 and those items decided exactly (k_res_nodes, k_res_tri).
+// pot32 / seg: the chunk's FP32 records; pot64: all samples' FP64 records.
+cudaError_t launch_resolve64(const Pot64* pot64, const Pot32* pot32, const Seg32* seg, int n_pot,
+                             const SampleGrid* grids, Sources src, Work64* work,
+                             const unsigned long long* work_count, int n_samples,
+                             int64_t work_cap, Hit* hits, int64_t hit_cap,
                              unsigned long long* hit_count, long long* counters,
                              uint32_t* status, ResolveScratch rs, int sm_count,
                              cudaStream_t st);
+// The tight FP32 stage of the resolution (k_res_tight32, k_res_tri32).
+cudaError_t launch_tight32(const Pot32* pot32, const Seg32* seg, int n_pot,
+                           const SampleGrid* grids, Sources src, Work64* work,
+                           const unsigned long long* work_count, int n_samples, int64_t work_cap,
+                           Hit* hits, int64_t hit_cap, unsigned long long* hit_count,
+                           long long* counters, uint32_t* status, ResolveScratch rs,
+                           int sm_count, cudaStream_t st);
 cudaError_t launch_sort_hits(const Hit* hits, const unsigned long long* hit_count, int n_samples,
                              int64_t hit_cap, int sample_base, lt_image* out, int64_t out_cap,
                              int64_t* n_out, uint32_t* status, cudaStream_t st);

@@ -87,13 +87,13 @@ __global__ void __launch_bounds__(kNT, kMinBlocks)
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
     // the batched kernel's body: the same operations in the same order
-    deflect32_nodes<kNT, kNPT>(pot32, n_pot, sg, theta1, X, Y, sp, AX, AY, ER);
+    deflect32_nodes<kNT, kNPT, true>(pot32, n_pot, sg, theta1, X, Y, sp, AX, AY, ER);
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {
       if (live && j0 + m < g.ny) {
         const int64_t n = (int64_t)(j0 + m) * g.nx + i;
         alpha[n] = make_float2(AX[m], AY[m]);
-        if (err) err[n] = node_bound(__fadd_ru(ER[m], sg.q_tot));
+        if (err) err[n] = node_bound(__fadd_ru(ER[m], sg.q_tot), n_pot);
       }
     }
   }

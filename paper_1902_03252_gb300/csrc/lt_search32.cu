@@ -440,4 +440,189 @@ cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- tight FP32 resolution
+// The search certifies with the coarse node bound.  The work items it leaves
+// undecided (and its certain hits whose position bound is too large) are
+// re-evaluated here before any FP64 work: every distinct node of those items
+// gets its FP32 deflection with the tight bound (k_res_tight32), and every
+// item is classified again with the search's own arithmetic (k_res_tri32).
+// Items decided there are done; the others list their nodes for the FP64
+// stage.
+//
+// k_res_tight32: one warp per node.  Lane l sums potentials l, l + 32, ...
+// (kind-sorted order) with the tight per-term and running-sum bound terms,
+// and the lanes' sums are combined by a butterfly of shuffles; every sum of
+// the butterfly is one rounding per component, charged |SX| + |SY|, and the
+// lanes' bound terms are summed along.  (IEEE addition is commutative, so
+// both lanes of a pair form the same sum and every lane ends with the same
+// total.)  The deflection differs from the deflection kernels' by the
+// summation order; the bound is that of this evaluation, which is the one
+// k_res_tri32 classifies with.
+constexpr int kTightThreads = 128;
+
+__global__ void __launch_bounds__(kTightThreads)
+    k_res_tight32(const Pot32* __restrict__ pot32, const Seg32* __restrict__ seg, int n_pot,
+                  const SampleGrid* __restrict__ grids, const unsigned long long* __restrict__ keys,
+                  const int32_t* __restrict__ ulist, const unsigned int* __restrict__ n_unique,
+                  float4* __restrict__ tval, long long* counters) {
+  grid_dependency_wait();
+  const unsigned int nu = *n_unique;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nu)
+    atomicAdd((unsigned long long*)&counters[CNT_TIGHT_NODES], (unsigned long long)nu);
+  const int lane = threadIdx.x & 31;
+  const unsigned int warps = gridDim.x * (kTightThreads / 32);
+  for (unsigned int t = blockIdx.x * (kTightThreads / 32) + (threadIdx.x >> 5); t < nu;
+       t += warps) {
+    const int32_t slot = ulist[t];
+    const unsigned long long key = keys[slot];
+    const int b = (int)(key >> 40);
+    const int64_t node = (int64_t)(key & ((1ull << 40) - 1));
+    const SampleGrid g = grids[b];
+    const Seg32 sg = seg[b];
+    const int j = (int)(node / g.nx), i = (int)(node - (int64_t)j * g.nx);
+    // the node coordinates of the deflection kernels: rounded once from FP64
+    const float X = (float)(g.x0 + (double)i * g.dx);
+    const float Yv[1] = {(float)(g.y0 + (double)j * g.dy)};
+    const Pot32* pb = pot32 + (int64_t)b * n_pot;
+    float PX[1] = {0.0f}, PY[1] = {0.0f}, ER[1] = {0.0f};
+    for (int k = lane; k < n_pot; k += 32) {
+      const Pot32 r = pb[k];
+      if (k < sg.n_sis)
+        sis32_nodes<1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
+      else if (k < sg.n_sis + sg.n_piemd)
+        piemd32_nodes<1, true>(r.f, stage_p32(r, true, g.theta_max), X, Yv, PX, PY, ER);
+      else
+        sie32_nodes<1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
+    }
+    float sx = PX[0], sy = PY[0], er = ER[0];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      er += __shfl_xor_sync(0xffffffffu, er, o);
+      er += fabsf(sx) + fabsf(sy);
+    }
+    if (lane == 0)
+      tval[slot] = make_float4(sx, sy, node_bound(__fadd_ru(er, sg.q_tot), n_pot), 0.0f);
+  }
+}
+
+// Vertex v (0, 1, 2) of triangle tri: cell (i, j) = (tri/2 mod (nx-1),
+// tri/2 div (nx-1)); T0 = (v00, v10, v11), T1 = (v00, v11, v01).
+__device__ __forceinline__ void tri_vertex32(int nx, int64_t tri, int v, int& i, int& j) {
+  const int64_t cell = tri / 2;
+  const int t = (int)(tri % 2);
+  i = (int)(cell % (nx - 1)) + (v == 0 ? 0 : (v == 1 ? 1 : (t == 0 ? 1 : 0)));
+  j = (int)(cell / (nx - 1)) + (v == 0 ? 0 : (v == 1 ? (t == 0 ? 0 : 1) : 1));
+}
+
+__global__ void k_res_tri32(const SampleGrid* __restrict__ grids, Sources src,
+                            Work64* __restrict__ work, const unsigned long long* __restrict__ work_count,
+                            int n_samples, int64_t work_cap, const int32_t* __restrict__ vslot,
+                            const float4* __restrict__ tval, Hit* __restrict__ hits,
+                            int64_t hit_cap, unsigned long long* hit_count, long long* counters,
+                            uint32_t* status, uint32_t* __restrict__ flag64,
+                            int32_t* __restrict__ ulist64, unsigned int* __restrict__ n64) {
+  grid_dependency_wait();
+  const float u = kU32;
+  long long n_hit = 0, n_left = 0;
+  const int64_t total = (int64_t)n_samples * work_cap;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(f / work_cap);
+    const int64_t idx = f - (int64_t)b * work_cap;
+    const unsigned long long cnt = work_count[b];
+    if ((unsigned long long)idx >= (cnt < (unsigned long long)work_cap ? cnt : work_cap)) continue;
+    const Work64 wk = work[f];
+    const SampleGrid g = grids[b];
+    // the source as the search stages it
+    const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
+    const float px = (float)sxy[2 * wk.src], py = (float)sxy[2 * wk.src + 1];
+    const float r = (float)src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
+    const float mu0 = __fmul_ru(u, __fmaf_ru(4.0f, g.theta_max, __fadd_ru(fabsf(px), fabsf(py))));
+    float ax[3], ay[3], mv[3];
+    bool ok = true;
+    for (int v = 0; v < 3; ++v) {
+      const int32_t slot = vslot[f * 3 + v];
+      if (slot < 0) { ok = false; break; }
+      int i, j;
+      tri_vertex32(g.nx, wk.tri, v, i, j);
+      const float4 a = tval[slot];
+      // relative mapped vertex and its bound, exactly as in the search
+      const float dx = fmaf((float)i, g.dxf, g.x0f) - px;
+      const float dy = fmaf((float)j, g.dyf, g.y0f) - py;
+      ax[v] = fmaf(-r, a.x, dx);
+      ay[v] = fmaf(-r, a.y, dy);
+      mv[v] = mu_up(__fmaf_ru(
+          r, a.z,
+          __fmaf_ru(u * 2.0f, __fmaf_ru(r, __fadd_ru(fabsf(a.x), fabsf(a.y)),
+                                        __fadd_ru(fabsf(dx), fabsf(dy))),
+                    mu0)));
+    }
+    if (!ok) {  // cannot happen with the table sized as it is; recorded, never silent
+      atomicOr(status, ST_OVERFLOW_WORK);
+      continue;
+    }
+    float w[3], pe = 0.0f;
+    const int cls = classify32(ax[0], ay[0], ax[1], ay[1], ax[2], ay[2], mv[0], mv[1], mv[2], w,
+                               &pe);
+    const float hmax = fmaxf(fabsf(g.dxf), fabsf(g.dyf));
+    bool done = cls == 0;
+    if (cls == 1 && pe * hmax <= (float)LT_POS_TOL) {
+      const int64_t cell = wk.tri / 2;
+      const int t = (int)(wk.tri % 2);
+      const int ci = (int)(cell % (g.nx - 1)), cj = (int)(cell / (g.nx - 1));
+      Hit h;
+      h.src = wk.src;
+      h.fp64 = 0;
+      h.tri = wk.tri;
+      h.w[0] = w[0]; h.w[1] = w[1]; h.w[2] = w[2];
+      const double2 xy = hit_xy(g.x0, g.y0, g.dx, g.dy, ci, cj, t, w[1], w[2]);
+      h.x = xy.x;
+      h.y = xy.y;
+      const unsigned long long k = atomicAdd(hit_count + b, 1ull);
+      if (k < (unsigned long long)hit_cap) hits[(int64_t)b * hit_cap + k] = h;
+      else atomicOr(status, ST_OVERFLOW_HITS);
+      ++n_hit;
+      done = true;
+    }
+    work[f].resolved = done ? 1 : 0;
+    if (!done) {
+      ++n_left;
+      for (int v = 0; v < 3; ++v) {
+        const int32_t slot = vslot[f * 3 + v];
+        if (atomicExch(&flag64[slot], 1u) == 0u) ulist64[atomicAdd(n64, 1u)] = slot;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    n_hit += __shfl_xor_sync(0xffffffffu, n_hit, o);
+    n_left += __shfl_xor_sync(0xffffffffu, n_left, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (n_hit) atomicAdd((unsigned long long*)&counters[CNT_HITS], (unsigned long long)n_hit);
+    if (n_left)
+      atomicAdd((unsigned long long*)&counters[CNT_FP64_ITEMS], (unsigned long long)n_left);
+  }
+}
+
+cudaError_t launch_tight32(const Pot32* pot32, const Seg32* seg, int n_pot,
+                           const SampleGrid* grids, Sources src, Work64* work,
+                           const unsigned long long* work_count, int n_samples, int64_t work_cap,
+                           Hit* hits, int64_t hit_cap, unsigned long long* hit_count,
+                           long long* counters, uint32_t* status, ResolveScratch rs,
+                           int sm_count, cudaStream_t st) {
+  // one warp per distinct node (at most three per item)
+  int64_t b1 = ((int64_t)n_samples * work_cap * 3 * 32 + kTightThreads - 1) / kTightThreads;
+  if (b1 > (int64_t)sm_count * 8) b1 = (int64_t)sm_count * 8;
+  cudaError_t e = launch_pdl(k_res_tight32, dim3((unsigned)b1), dim3(kTightThreads), st, pot32,
+                             seg, n_pot, grids, rs.keys, rs.ulist, rs.n_unique, rs.tval, counters);
+  if (e != cudaSuccess) return e;
+  int64_t b2 = ((int64_t)n_samples * work_cap + 127) / 128;
+  if (b2 > (int64_t)sm_count * 16) b2 = (int64_t)sm_count * 16;
+  return launch_pdl(k_res_tri32, dim3((unsigned)b2), dim3(128), st, grids, src, work, work_count,
+                    n_samples, work_cap, rs.vslot, rs.tval, hits, hit_cap, hit_count, counters,
+                    status, rs.flag64, rs.ulist64, rs.n64);
+}
+
 }  // namespace lt

@@ -53,7 +53,8 @@ class Obs(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("hits", C.c_int64), ("ambiguous", C.c_int64), ("refined", C.c_int64),
-                ("fp64_nodes", C.c_int64), ("work_overflow", C.c_int64)]
+                ("fp64_nodes", C.c_int64), ("work_overflow", C.c_int64),
+                ("tight_nodes", C.c_int64), ("fp64_items", C.c_int64)]
 
 
 class Profile(C.Structure):
