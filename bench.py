@@ -44,14 +44,23 @@ UNIT = "chi2_evals/s"
 WORKLOAD = ("c2: 100 PIEMD, 2000^2 grid over 200\", 20 systems / 72 observed images, "
             "one lens sample per chi^2 evaluation")
 SM_PER_GPU_FALLBACK = 152
-# Algorithmic work of one PIEMD node x potential evaluation (difference form):
-# 60 FP32 pipe operations and 8 MUFU operations; at 128 FP32 lanes and 16
-# MUFU lanes per SM per clock the FP32 pipe allows 2.1 and the MUFU pipe 2
-# node x potential per SM-clock: the roofline is the smaller, 2.  (The kernel
-# issues fewer instructions than 60 + 8 per node x potential, because most
-# range reductions are skipped; what limits it in practice is instruction
-# issue, about one warp instruction per clock per SM sub-partition.)
-PIEMD_NODE_POT_PER_SM_CLK = 2.0
+# Algorithmic work of one PIEMD node x potential evaluation (difference form,
+# counted from its formulas on the common path where both special functions
+# are their polynomials; the range reductions of a minority of node x
+# potentials are not counted): 46 FP32 pipe operations (translate 2, rotate 4,
+# squares 2, q^2 x^2 + y^2 1, psi_a^2 and psi_s^2 2, psi_a 1, psi_a + psi_s 1,
+# d_x and d_y 2, the two denominators' factors 6 and sums 2, t_x and t_y 4,
+# their squares 2, the two polynomials 6 + 4, g 2, rotation back and
+# accumulation 4, the bound term P / psi_a 1) and 5 MUFU operations (rsqrt for
+# psi_a, sqrt for psi_s, three reciprocals).  At 128 FP32 lanes and 16 MUFU
+# lanes per SM per clock the FP32 pipe allows 128 / 46 = 2.78 and the MUFU pipe
+# 3.2 node x potential per SM-clock: the FP32 pipe bounds the kernel.
+PIEMD_FP32_OPS = 46
+PIEMD_MUFU_OPS = 5
+FP32_LANES_PER_SM_CLK = 128.0
+MUFU_LANES_PER_SM_CLK = 16.0
+PIEMD_NODE_POT_PER_SM_CLK = min(FP32_LANES_PER_SM_CLK / PIEMD_FP32_OPS,
+                                MUFU_LANES_PER_SM_CLK / PIEMD_MUFU_OPS)
 # The plain FP64 form: GB300 runs FP64 at 1/64 of the FP32 rate, 2 FP64
 # lanes per SM per clock.  FP64 pipe operations per PIEMD node x potential,
 # counted from the formula (52 add/mul/sub, 6 sqrt, 8 div, 2 atan, 2 atanh)
@@ -528,8 +537,9 @@ def run_ours(a, rank, world, local):
                                        "null otherwise)",
                      "kernel": "k_deflect32", "kernel_ms": defl_ms,
                      "peak_basis": f"{sm_count} SMs x {f_max / 1e6:.0f} MHz (max SM clock) x "
-                                   "2 PIEMD node.pot per SM-clock (min of 128 FP32 / 60 "
-                                   "ops and 16 MUFU / 8 ops)"},
+                                   f"{PIEMD_NODE_POT_PER_SM_CLK:.3f} PIEMD node.pot per SM-clock "
+                                   f"(FP32 pipe: 128 lanes / {PIEMD_FP32_OPS} ops; the MUFU "
+                                   f"pipe allows 16 lanes / {PIEMD_MUFU_OPS} ops)"},
         "kernel_ms_per_step": breakdown,
         "stats": stats,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,

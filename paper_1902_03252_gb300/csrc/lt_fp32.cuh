@@ -62,42 +62,229 @@ __device__ __forceinline__ float stage_p32(const Pot32& r, bool piemd, float the
   return __fadd_ru(P, 1e-30f);
 }
 
+// ------------------------------------------------ explicit FP32 operations
+// The per-node arithmetic below is written once for a node lane type V:
+// float (one node) or F2 (two nodes of one thread, in the paired FP32
+// instructions add/sub/mul/fma .f32x2 of sm_100 and later, which do two
+// lanes' operations in one issue slot at the FP32 pipe's lane rate).  Every
+// operation is explicit (inline PTX, round to nearest, flush to zero), so a
+// node gets the same operations, roundings and results whether it sits in
+// a pair or alone: a thread's nodes are paired as far as they go, and an odd
+// last node runs the same code with V = float.  No operation is contracted
+// or reassociated by the compiler.  (Per-thread, per-potential scalars such
+// as the column's translation are ordinary float expressions; they do not
+// depend on the pairing.)
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ F2 f2_pack(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(F2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+
+__device__ __forceinline__ float xfma(float a, float b, float c) {
+  float d;
+  asm("fma.rn.ftz.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float xmul(float a, float b) {
+  float d;
+  asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float xadd(float a, float b) {
+  float d;
+  asm("add.rn.ftz.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float xsub(float a, float b) {
+  float d;
+  asm("sub.rn.ftz.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ F2 xfma(F2 a, F2 b, F2 c) {
+  F2 d;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
+__device__ __forceinline__ F2 xmul(F2 a, F2 b) {
+  F2 d;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ F2 xadd(F2 a, F2 b) {
+  F2 d;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ F2 xsub(F2 a, F2 b) {
+  F2 d;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+
+// lane access, broadcast and lane-wise maps (the MUFU approximations, the
+// rare range-reduced special functions, absolute values, selects)
+template <class V> struct Lanes;
+template <> struct Lanes<float> {
+  static constexpr int n = 1;
+  __device__ __forceinline__ static float bc(float a) { return a; }
+  __device__ __forceinline__ static float get(float a, int) { return a; }
+};
+template <> struct Lanes<F2> {
+  static constexpr int n = 2;
+  __device__ __forceinline__ static F2 bc(float a) { return f2_pack(a, a); }
+  __device__ __forceinline__ static float get(F2 a, int l) {
+    float lo, hi;
+    f2_unpack(a, lo, hi);
+    return l ? hi : lo;
+  }
+};
+template <class V, class Fn>
+__device__ __forceinline__ V lanewise(V a, Fn fn) {
+  if constexpr (Lanes<V>::n == 1) {
+    return fn(a);
+  } else {
+    float a0, a1;
+    f2_unpack(a, a0, a1);
+    return f2_pack(fn(a0), fn(a1));
+  }
+}
+template <class V> __device__ __forceinline__ V xrsqrt(V a) { return lanewise(a, rsqrt_approx32); }
+template <class V> __device__ __forceinline__ V xsqrt(V a) { return lanewise(a, sqrt_approx32); }
+template <class V> __device__ __forceinline__ V xrcp(V a) { return lanewise(a, rcp_approx32); }
+template <class V> __device__ __forceinline__ V xabs(V a) {
+  return lanewise(a, [](float x) { return fabsf(x); });
+}
+// per lane: a where x > thr, else b
+template <class V> __device__ __forceinline__ V xselect_gt(V x, float thr, V a, V b) {
+  if constexpr (Lanes<V>::n == 1) {
+    return x > thr ? a : b;
+  } else {
+    float x0, x1, a0, a1, b0, b1;
+    f2_unpack(x, x0, x1);
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    return f2_pack(x0 > thr ? a0 : b0, x1 > thr ? a1 : b1);
+  }
+}
+
+// r on lanes where R2 > 0, else 0 (the deflection is zero at an SIS/SIE centre)
+template <class V> __device__ __forceinline__ V xpos_or_zero(V R2, V r) {
+  return xselect_gt(R2, 0.0f, r, Lanes<V>::bc(0.0f));
+}
+
+// The polynomials of atanc_poly32 / atanhc_poly32 (the same coefficients, by
+// Horner's rule), on node lanes.
+template <class V> __device__ __forceinline__ V atanc_poly(V u) {
+  typedef Lanes<V> L;
+  V p = L::bc(7.685306482e-03f);
+  p = xfma(p, u, L::bc(-3.647336364e-02f));
+  p = xfma(p, u, L::bc(8.325644583e-02f));
+  p = xfma(p, u, L::bc(-1.345480382e-01f));
+  p = xfma(p, u, L::bc(1.987373084e-01f));
+  p = xfma(p, u, L::bc(-3.332583010e-01f));
+  return xfma(p, u, L::bc(9.999992251e-01f));
+}
+template <class V> __device__ __forceinline__ V atanhc_poly(V u) {
+  typedef Lanes<V> L;
+  V p = L::bc(1.953562647e-01f);
+  p = xfma(p, u, L::bc(1.221839786e-01f));
+  p = xfma(p, u, L::bc(2.019458860e-01f));
+  p = xfma(p, u, L::bc(3.332709372e-01f));
+  return xfma(p, u, L::bc(1.000000358e+00f));
+}
+
+// The range-reduced forms of atanc_reduced32 / atanhc_reduced32 on node
+// lanes, with the same operations in the same order (so every node gets the
+// values of the scalar functions): atan(t)/t for t2 > 1 and atanh(t)/t for
+// t2 > 1/4.
+template <class V> __device__ __forceinline__ V atanc_reduced(V t2) {
+  typedef Lanes<V> L;
+  const V r = xrsqrt(t2);
+  const V inv = xmul(r, r);
+  const V pinv = xmul(atanc_poly(inv), inv);
+  return xfma(L::bc(1.57079633f), r, xmul(L::bc(-1.0f), pinv));  // pi/2 r - p inv
+}
+template <class V> __device__ __forceinline__ V atanhc_reduced(V t2) {
+  typedef Lanes<V> L;
+  const V tc = lanewise(t2, [](float x) { return fminf(x, 0.99999988f); });
+  const V r = xrsqrt(tc);
+  const V num = xfma(tc, r, L::bc(1.0f));
+  const V den = xfma(xmul(L::bc(-1.0f), tc), r, L::bc(1.0f));
+  const V ratio = xmul(num, xrcp(den));
+  return xmul(xmul(lanewise(ratio, lg2_approx32), L::bc(0.5f * 0.693147181f)), r);
+}
+
+// The largest of the NV node lanes' values (three-input max of sm_100 and
+// later).  Used only to test whether any lane exceeds a threshold; a NaN lane
+// never counts as exceeding it, as with x > thr.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+template <class V, int NV> __device__ __forceinline__ float lanes_max(const V* v) {
+  if constexpr (Lanes<V>::n == 1) {
+    float m = v[0];
+#pragma unroll
+    for (int i = 1; i < NV; ++i) m = fmaxf(m, v[i]);
+    return m;
+  } else {
+    float m, a, b;
+    f2_unpack(v[0], m, a);
+    m = fmaxf(m, a);
+#pragma unroll
+    for (int i = 1; i < NV; ++i) {
+      f2_unpack(v[i], a, b);
+      m = max3f(m, a, b);
+    }
+    return m;
+  }
+}
+
 // Add a group's partial sums to the totals (one rounding per component,
 // bounded by the new total) and clear them.
-template <int NPT, bool TIGHT>
-__device__ __forceinline__ void flush_group(float* AX, float* AY, float* PX, float* PY,
-                                            float* ER) {
+template <class V, int NV, bool TIGHT>
+__device__ __forceinline__ void flush_group(V* AX, V* AY, V* PX, V* PY, V* ER) {
+  typedef Lanes<V> L;
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
-    AX[m] += PX[m];
-    AY[m] += PY[m];
-    if (TIGHT) ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
-    PX[m] = 0.0f;
-    PY[m] = 0.0f;
+  for (int m = 0; m < NV; ++m) {
+    AX[m] = xadd(AX[m], PX[m]);
+    AY[m] = xadd(AY[m], PY[m]);
+    if (TIGHT) ER[m] = xfma(L::bc(2.0f), xadd(xabs(AX[m]), xabs(AY[m])), ER[m]);
+    PX[m] = L::bc(0.0f);
+    PY[m] = L::bc(0.0f);
   }
 }
 
 // One SIS: alpha += b0 (theta - c)/R (zero at the centre).  err accumulates in
 // units of the FP32 unit roundoff.  In this and the two functions below, AX
-// and AY are a group's partial sums (flush_group).
-template <int NPT, bool TIGHT>
-__device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, const float* Y,
-                                            float* AX, float* AY, float* ER) {
+// and AY are a group's partial sums (flush_group), NV node lanes of type V
+// at the column X and the rows Y[].
+template <class V, int NV, bool TIGHT>
+__device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, const V* Y,
+                                            V* AX, V* AY, V* ER) {
+  typedef Lanes<V> L;
   const float dx = X - f[0].x;
   const float dx2 = dx * dx;
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
-    const float dy = Y[m] - f[0].y;
-    const float R2 = fmaf(dy, dy, dx2);
+  for (int m = 0; m < NV; ++m) {
+    const V dy = xsub(Y[m], L::bc(f[0].y));
+    const V R2 = xfma(dy, dy, L::bc(dx2));
     // rr is +inf on the centre: there the direction of alpha is undefined and
     // the bound term P rr makes the node's bound infinite (never certified)
-    const float rr = rsqrt_approx32(R2);
-    const float ri = R2 > 0.0f ? rr : 0.0f;
-    const float g = f[0].z * ri;
-    AX[m] = fmaf(g, dx, AX[m]);
-    AY[m] = fmaf(g, dy, AY[m]);
-    ER[m] = fmaf(P, rr, ER[m]);
-    if (TIGHT) ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+    const V rr = xrsqrt(R2);
+    const V ri = xpos_or_zero(R2, rr);
+    const V g = xmul(L::bc(f[0].z), ri);
+    AX[m] = xfma(g, L::bc(dx), AX[m]);
+    AY[m] = xfma(g, dy, AY[m]);
+    ER[m] = xfma(L::bc(P), rr, ER[m]);
+    if (TIGHT) ER[m] = xfma(L::bc(2.0f), xadd(xabs(AX[m]), xabs(AY[m])), ER[m]);
   }
 }
 
@@ -111,25 +298,26 @@ __device__ __forceinline__ void sis32_nodes(const float4* f, float P, float X, c
 // f[0] = {cx, cy, sqrt(1-eps) c, sqrt(1-eps) s},
 // f[1] = {sqrt(1+eps) c, sqrt(1+eps) s, b0 sqrt(1-eps) c, b0 sqrt(1+eps) s},
 // f[2] = {b0 sqrt(1+eps) c, b0 sqrt(1-eps) s, 0, 0}.
-template <int NPT, bool TIGHT>
-__device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, const float* Y,
-                                            float* AX, float* AY, float* ER) {
+template <class V, int NV, bool TIGHT>
+__device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, const V* Y,
+                                            V* AX, V* AY, V* ER) {
+  typedef Lanes<V> L;
   const float dx = X - f[0].x;
-  const float dxu = dx * f[0].z, dxv = dx * f[1].y;
+  const float dxu = dx * f[0].z, ndxv = -dx * f[1].y;
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
-    const float dy = Y[m] - f[0].y;
-    const float u = fmaf(dy, f[0].w, dxu);
-    const float v = fmaf(dy, f[1].x, -dxv);
-    const float R2 = fmaf(u, u, v * v);
-    const float rr = rsqrt_approx32(R2);  // +inf on the centre: an infinite bound there
-    const float ri = R2 > 0.0f ? rr : 0.0f;
-    const float t1 = fmaf(f[1].z, u, -(f[1].w * v));
-    const float t2 = fmaf(f[2].x, v, f[2].y * u);
-    AX[m] = fmaf(ri, t1, AX[m]);
-    AY[m] = fmaf(ri, t2, AY[m]);
-    ER[m] = fmaf(P, rr, ER[m]);
-    if (TIGHT) ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+  for (int m = 0; m < NV; ++m) {
+    const V dy = xsub(Y[m], L::bc(f[0].y));
+    const V u = xfma(dy, L::bc(f[0].w), L::bc(dxu));
+    const V v = xfma(dy, L::bc(f[1].x), L::bc(ndxv));
+    const V R2 = xfma(u, u, xmul(v, v));
+    const V rr = xrsqrt(R2);  // +inf on the centre: an infinite bound there
+    const V ri = xpos_or_zero(R2, rr);
+    const V t1 = xfma(L::bc(f[1].z), u, xmul(L::bc(-f[1].w), v));
+    const V t2 = xfma(L::bc(f[2].x), v, xmul(L::bc(f[2].y), u));
+    AX[m] = xfma(ri, t1, AX[m]);
+    AY[m] = xfma(ri, t2, AY[m]);
+    ER[m] = xfma(L::bc(P), rr, ER[m]);
+    if (TIGHT) ER[m] = xfma(L::bc(2.0f), xadd(xabs(AX[m]), xabs(AY[m])), ER[m]);
   }
 }
 
@@ -140,81 +328,83 @@ __device__ __forceinline__ void sie32_nodes(const float4* f, float P, float X, c
 // ds_x = (s-a)(1 + q^2 (s+a)/(psi_a+psi_s)), ds_y = q^2 (s-a)(1 + (s+a)/(psi_a+psi_s))
 // (atan u - atan v = atan((u-v)/(1+uv)), atanh likewise, and
 // psi_s - psi_a = q^2 (s^2-a^2)/(psi_a+psi_s)), which avoids the cancellation
-// of the two cored terms and halves the transcendental work.
+// of the two cored terms and halves the transcendental work.  psi_a enters
+// the sums as the fused psi_a^2 rsqrt(psi_a^2) + z (one rounding each).
 //
-// One PIEMD on the NPT nodes of a thread (one column).  The range tests of
-// the two special functions are merged into one branch per thread and
-// potential: both polynomials of atanc_sq32 / atanhc_sq32 are evaluated on
-// the unreduced arguments for every node (out of range the value may
-// overflow; it is replaced), and the nodes outside their ranges (atan:
-// t2 > 1, atanh: t2 > 0.25; about 14 % of node-potential pairs on cluster
-// lenses) are then recomputed by those functions.  Every node gets exactly
-// the values and roundings of the per-node evaluation; the merged test
-// removes most of the branch instructions from the issue stream.
-template <int NPT, bool TIGHT>
-__device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X, const float* Y,
-                                              float* AX, float* AY, float* ER) {
-  const float cy = f[0].y, c = f[0].z, s = f[0].w;
-  const float k2 = f[1].w, Bc = f[3].w, Bs = f[4].w;
+// The range tests of the two special functions are one branch per thread,
+// potential and function: both polynomials are evaluated on the unreduced
+// arguments for every node (out of range the value may overflow; it is
+// replaced), and where any of the thread's nodes is outside a range (atan:
+// t2 > 1, about 1 % of a warp's potentials on cluster lenses; atanh:
+// t2 > 0.25, about 15 %) the reduced form is evaluated for all its nodes and
+// selected per node.  Every node gets exactly the values and roundings of
+// atanc_sq32 / atanhc_sq32; the per-thread tests keep the branches out of
+// most of the issue stream.
+template <class V, int NV, bool TIGHT>
+__device__ __forceinline__ void piemd32_nodes(const float4* f, float P, float X, const V* Y,
+                                              V* AX, V* AY, V* ER) {
+  typedef Lanes<V> L;
   const float dx = X - f[0].x;
-  const float dxc = dx * c, dxs = dx * s;
-  float tx[NPT], ty[NPT], ux[NPT], uy[NPT], ra[NPT], px_[NPT], py_[NPT];
-  bool any = false;
+  const float dxc = dx * f[0].z, ndxs = -dx * f[0].w;
+  V tx[NV], ty[NV], ux[NV], uy[NV], ra[NV];
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
-    const float dy = Y[m] - cy;
-    const float xp = fmaf(dy, s, dxc);
-    const float yp = fmaf(dy, c, -dxs);
-    const float x2 = xp * xp, y2 = yp * yp;
-    const float t = fmaf(f[1].x, x2, y2);
-    const float pa2 = t + f[1].y, ps2 = t + f[1].z;
-    ra[m] = rsqrt_approx32(pa2);
+  for (int m = 0; m < NV; ++m) {
+    const V dy = xsub(Y[m], L::bc(f[0].y));
+    const V xp = xfma(dy, L::bc(f[0].w), L::bc(dxc));
+    const V yp = xfma(dy, L::bc(f[0].z), L::bc(ndxs));
+    const V x2 = xmul(xp, xp), y2 = xmul(yp, yp);
+    const V t = xfma(L::bc(f[1].x), x2, y2);
+    const V pa2 = xadd(t, L::bc(f[1].y)), ps2 = xadd(t, L::bc(f[1].z));
+    ra[m] = xrsqrt(pa2);
     // psi_s in one MUFU operation.  Over every float mantissa (four binades
     // checked exhaustively on GB300) sqrt.approx.ftz errs by at most 1.68 u
     // against the rounded sqrt, below the 2.71 u of ps2 * rsqrt(ps2) that the
     // error bound was derived for; psi_a keeps that form, as 1/psi_a is needed.
-    const float ps = sqrt_approx32(ps2);
-    const float pa = pa2 * ra[m];
-    const float iD = rcp_approx32(pa + ps);
-    const float dsx = fmaf(f[3].y, iD, f[3].x);
-    const float dsy = fmaf(f[3].y, iD, f[3].z);
-    const float px = (pa + f[2].x) * (ps + f[2].y);
-    const float py = (pa + f[2].z) * (ps + f[2].w);
-    const float denx = fmaf(k2, x2, px);
-    const float deny = fmaf(-k2, y2, py);
+    const V ps = xsqrt(ps2);
+    const V iD = xrcp(xfma(pa2, ra[m], ps));
+    const V dsx = xfma(L::bc(f[3].y), iD, L::bc(f[3].x));
+    const V dsy = xfma(L::bc(f[3].y), iD, L::bc(f[3].z));
+    const V px = xmul(xfma(pa2, ra[m], L::bc(f[2].x)), xadd(ps, L::bc(f[2].y)));
+    const V py = xmul(xfma(pa2, ra[m], L::bc(f[2].z)), xadd(ps, L::bc(f[2].w)));
+    const V denx = xfma(L::bc(f[1].w), x2, px);
+    const V deny = xfma(L::bc(-f[1].w), y2, py);
     // the ds coefficients carry sig = sqrt(k2): these are sig tx, sig ty
-    tx[m] = (xp * dsx) * rcp_approx32(denx);
-    ty[m] = (yp * dsy) * rcp_approx32(deny);
-    ux[m] = tx[m] * tx[m];
-    uy[m] = ty[m] * ty[m];
-    any |= (ux[m] > 1.0f) | (uy[m] > 0.25f);
+    tx[m] = xmul(xmul(xp, dsx), xrcp(denx));
+    ty[m] = xmul(xmul(yp, dsy), xrcp(deny));
+    ux[m] = xmul(tx[m], tx[m]);
+    uy[m] = xmul(ty[m], ty[m]);
+    ER[m] = xfma(L::bc(P), ra[m], ER[m]);
   }
+  V px_[NV], py_[NV];
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
+  for (int m = 0; m < NV; ++m) {
     // the polynomials of atanc_sq32 / atanhc_sq32 on the unreduced arguments
-    const float p = atanc_poly32(ux[m]);
-    const float h = atanhc_poly32(uy[m]);
-    px_[m] = p;
-    py_[m] = h;
+    px_[m] = atanc_poly(ux[m]);
+    py_[m] = atanhc_poly(uy[m]);
   }
-  if (any) {
+  // every node's reduced form, kept where its argument is out of range: one
+  // select per node, each pair rebuilt whole (no register of a pair is
+  // written under a branch)
+  if (lanes_max<V, NV>(ux) > 1.0f) {
 #pragma unroll
-    for (int m = 0; m < NPT; ++m) {
-      if (ux[m] > 1.0f) px_[m] = atanc_sq32(ux[m]);
-      if (uy[m] > 0.25f) py_[m] = atanhc_sq32(uy[m]);
-    }
+    for (int m = 0; m < NV; ++m) px_[m] = xselect_gt(ux[m], 1.0f, atanc_reduced(ux[m]), px_[m]);
   }
+  if (lanes_max<V, NV>(uy) > 0.25f) {
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
+    for (int m = 0; m < NV; ++m)
+      py_[m] = xselect_gt(uy[m], 0.25f, atanhc_reduced(uy[m]), py_[m]);
+  }
+  const V Bc = L::bc(f[3].w), Bs = L::bc(f[4].w), nBs = L::bc(-f[4].w);
+#pragma unroll
+  for (int m = 0; m < NV; ++m) {
     // the rotated-frame components are (B/sig) gx, (B/sig) gy
-    const float gx = tx[m] * px_[m];
-    const float gy = ty[m] * py_[m];
-    AX[m] = fmaf(gx, Bc, fmaf(-gy, Bs, AX[m]));
-    AY[m] = fmaf(gy, Bc, fmaf(gx, Bs, AY[m]));
-    ER[m] = fmaf(P, ra[m], ER[m]);
+    const V gx = xmul(tx[m], px_[m]);
+    const V gy = xmul(ty[m], py_[m]);
+    AX[m] = xfma(gx, Bc, xfma(gy, nBs, AX[m]));
+    AY[m] = xfma(gy, Bc, xfma(gx, Bs, AY[m]));
     if (TIGHT) {
-      ER[m] = fmaf(f[4].y, fabsf(gx), fmaf(f[4].z, fabsf(gy), ER[m]));
-      ER[m] = fmaf(2.0f, fabsf(AX[m]) + fabsf(AY[m]), ER[m]);
+      ER[m] = xfma(L::bc(f[4].y), xabs(gx), xfma(L::bc(f[4].z), xabs(gy), ER[m]));
+      ER[m] = xfma(L::bc(2.0f), xadd(xabs(AX[m]), xabs(AY[m])), ER[m]);
     }
   }
 }
@@ -236,26 +426,56 @@ __device__ __forceinline__ void stage_chunk32(float4* sp, const Pot32* __restric
   }
 }
 
+// The node lanes of one thread: its NPT nodes as NPT / 2 pairs (F2) and, for
+// odd NPT, one single node (float).
+template <int NPT>
+struct NodeLanes {
+  static constexpr int NP = NPT / 2;
+  static constexpr bool ODD = (NPT % 2) != 0;
+  F2 p[NP > 0 ? NP : 1];
+  float s[1];
+};
+
+// Apply one kind's per-potential function KF to a thread's node lanes.
+#define LT_NODES_APPLY(KF, TIGHT, f, P, X, Y, AX, AY, ER)                              \
+  do {                                                                                \
+    if constexpr (decltype(Y)::NP > 0)                                                \
+      KF<F2, decltype(Y)::NP, TIGHT>(f, P, X, Y.p, AX.p, AY.p, ER.p);                  \
+    if constexpr (decltype(Y)::ODD) KF<float, 1, TIGHT>(f, P, X, Y.s, AX.s, AY.s, ER.s); \
+  } while (0)
+
+template <int NPT, bool TIGHT>
+__device__ __forceinline__ void flush_lanes(NodeLanes<NPT>& AX, NodeLanes<NPT>& AY,
+                                            NodeLanes<NPT>& PX, NodeLanes<NPT>& PY,
+                                            NodeLanes<NPT>& ER) {
+  constexpr int NP = NodeLanes<NPT>::NP;
+  if constexpr (NP > 0) flush_group<F2, NP, TIGHT>(AX.p, AY.p, PX.p, PY.p, ER.p);
+  if constexpr (NodeLanes<NPT>::ODD) flush_group<float, 1, TIGHT>(AX.s, AY.s, PX.s, PY.s, ER.s);
+}
+
 // The per-item body of both FP32 deflection kernels: the deflection (AX, AY)
 // and the running-bound terms ER (tight or coarse) of one thread's NPT nodes (column X, rows
 // Y[]) over all n_pot potentials of one sample, kind segment by kind segment
 // ([0, n_sis) SIS, then PIEMD, then SIE), in groups of at most kSumGroup
 // potentials whose partial sums join the totals once per group.  The order of
-// every operation of a node depends only on the potentials, not on NT or NPT.
+// every operation of a node depends only on the potentials, not on NT, NPT or
+// the pairing of the thread's nodes.
 // sp: shared memory of kChunk32 * 5 float4; called by all NT threads.
 template <int NT, int NPT, bool TIGHT>
 __device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, int n_pot,
                                                 const Seg32& sg, float theta1, float X,
                                                 const float* Y, float4* sp, float* AX,
                                                 float* AY, float* ER) {
-  float PX[NPT], PY[NPT];
+  typedef NodeLanes<NPT> NL;
+  NL y, ax, ay, px, py, er;
 #pragma unroll
-  for (int m = 0; m < NPT; ++m) {
-    PX[m] = 0.0f;
-    PY[m] = 0.0f;
-    AX[m] = 0.0f;
-    AY[m] = 0.0f;
-    ER[m] = 0.0f;
+  for (int m = 0; m < NL::NP; ++m) {
+    y.p[m] = f2_pack(Y[2 * m], Y[2 * m + 1]);
+    ax.p[m] = ay.p[m] = px.p[m] = py.p[m] = er.p[m] = f2_pack(0.0f, 0.0f);
+  }
+  if constexpr (NL::ODD) {
+    y.s[0] = Y[NPT - 1];
+    ax.s[0] = ay.s[0] = px.s[0] = py.s[0] = er.s[0] = 0.0f;
   }
   for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
     const int cn = min(kChunk32, n_pot - c0);
@@ -266,20 +486,32 @@ __device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, in
     const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
     for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {
       for (int k = k0; k < min(k0 + kSumGroup, e_sis); ++k)
-        sis32_nodes<NPT, TIGHT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-      flush_group<NPT, TIGHT>(AX, AY, PX, PY, ER);
+        LT_NODES_APPLY(sis32_nodes, TIGHT, &sp[k * 5], sp[k * 5 + 4].x, X, y, px, py, er);
+      flush_lanes<NPT, TIGHT>(ax, ay, px, py, er);
     }
     for (int k0 = e_sis; k0 < e_pie; k0 += kSumGroup) {
       for (int k = k0; k < min(k0 + kSumGroup, e_pie); ++k)
-        piemd32_nodes<NPT, TIGHT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-      flush_group<NPT, TIGHT>(AX, AY, PX, PY, ER);
+        LT_NODES_APPLY(piemd32_nodes, TIGHT, &sp[k * 5], sp[k * 5 + 4].x, X, y, px, py, er);
+      flush_lanes<NPT, TIGHT>(ax, ay, px, py, er);
     }
     for (int k0 = e_pie; k0 < cn; k0 += kSumGroup) {
       for (int k = k0; k < min(k0 + kSumGroup, cn); ++k)
-        sie32_nodes<NPT, TIGHT>(&sp[k * 5], sp[k * 5 + 4].x, X, Y, PX, PY, ER);
-      flush_group<NPT, TIGHT>(AX, AY, PX, PY, ER);
+        LT_NODES_APPLY(sie32_nodes, TIGHT, &sp[k * 5], sp[k * 5 + 4].x, X, y, px, py, er);
+      flush_lanes<NPT, TIGHT>(ax, ay, px, py, er);
     }
   }
+#pragma unroll
+  for (int m = 0; m < NL::NP; ++m) {
+    f2_unpack(ax.p[m], AX[2 * m], AX[2 * m + 1]);
+    f2_unpack(ay.p[m], AY[2 * m], AY[2 * m + 1]);
+    f2_unpack(er.p[m], ER[2 * m], ER[2 * m + 1]);
+  }
+  if constexpr (NL::ODD) {
+    AX[NPT - 1] = ax.s[0];
+    AY[NPT - 1] = ay.s[0];
+    ER[NPT - 1] = er.s[0];
+  }
 }
+#undef LT_NODES_APPLY
 
 }  // namespace lt

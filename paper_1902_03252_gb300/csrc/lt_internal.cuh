@@ -290,23 +290,32 @@ __device__ __forceinline__ float atanhc_poly32(float u) {
 // there, away from lg2's absolute-error range around 1).
 // The largest relative errors of both functions over all their float
 // arguments are measured on the GPU (tests/test_gpu_special.py).
+// The range-reduced forms alone (no test; valid for t2 > 1 and t2 > 1/4
+// respectively, finite or not elsewhere): the deflection kernels evaluate
+// them for all of a thread's nodes and select per node, so no register of a
+// node pair is updated under a branch.  Every operation is written out
+// (__fmaf_rn / __fmul_rn are never contracted or split), so the deflection
+// kernels' lane forms (lt_fp32.cuh) repeat them exactly.
+__device__ __forceinline__ float atanc_reduced32(float t2) {
+  const float r = rsqrt_approx32(t2);
+  const float inv = __fmul_rn(r, r);
+  const float p = atanc_poly32(inv);
+  return __fmaf_rn(1.57079633f, r, -__fmul_rn(p, inv));
+}
+__device__ __forceinline__ float atanhc_reduced32(float t2) {
+  t2 = fminf(t2, 0.99999988f);
+  const float r = rsqrt_approx32(t2);
+  // 1 + t and 1 - t with t = t2 r, each one fused multiply-add
+  const float num = __fmaf_rn(t2, r, 1.0f), den = __fmaf_rn(-t2, r, 1.0f);
+  return __fmul_rn(__fmul_rn(lg2_approx32(__fmul_rn(num, rcp_approx32(den))),
+                             0.5f * 0.693147181f),
+                   r);
+}
 __device__ __forceinline__ float atanc_sq32(float t2) {
-  if (t2 > 1.0f) {
-    const float r = rsqrt_approx32(t2);
-    const float inv = r * r;
-    const float p = atanc_poly32(inv);
-    return fmaf(1.57079633f, r, -(p * inv));
-  }
-  return atanc_poly32(t2);
+  return t2 > 1.0f ? atanc_reduced32(t2) : atanc_poly32(t2);
 }
 __device__ __forceinline__ float atanhc_sq32(float t2) {
-  if (t2 > 0.25f) {
-    t2 = fminf(t2, 0.99999988f);
-    const float r = rsqrt_approx32(t2);
-    const float t = t2 * r;
-    return lg2_approx32((1.0f + t) * rcp_approx32(1.0f - t)) * (0.5f * 0.693147181f) * r;
-  }
-  return atanhc_poly32(t2);
+  return t2 > 0.25f ? atanhc_reduced32(t2) : atanhc_poly32(t2);
 }
 
 // Launch-shape variants of the FP32 deflection kernel (autotuned).
@@ -318,7 +327,7 @@ struct DeflectShape {
 constexpr int kNumShapes = 8;
 __host__ __device__ constexpr DeflectShape deflect_shape(int v) {
   const DeflectShape tab[kNumShapes] = {{256, 4, 3}, {256, 2, 5}, {256, 3, 4}, {128, 8, 3},
-                                        {128, 8, 4}, {128, 4, 7}, {128, 4, 8}, {256, 2, 6}};
+                                        {128, 8, 4}, {128, 4, 7}, {128, 4, 4}, {256, 4, 2}};
   return tab[v < 0 || v >= kNumShapes ? 0 : v];
 }
 

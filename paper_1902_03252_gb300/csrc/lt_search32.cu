@@ -488,11 +488,11 @@ __global__ void __launch_bounds__(kTightThreads)
     for (int k = lane; k < n_pot; k += 32) {
       const Pot32 r = pb[k];
       if (k < sg.n_sis)
-        sis32_nodes<1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
+        sis32_nodes<float, 1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
       else if (k < sg.n_sis + sg.n_piemd)
-        piemd32_nodes<1, true>(r.f, stage_p32(r, true, g.theta_max), X, Yv, PX, PY, ER);
+        piemd32_nodes<float, 1, true>(r.f, stage_p32(r, true, g.theta_max), X, Yv, PX, PY, ER);
       else
-        sie32_nodes<1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
+        sie32_nodes<float, 1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
     }
     float sx = PX[0], sy = PY[0], er = ER[0];
 #pragma unroll

@@ -141,6 +141,43 @@ def test_deflect_bound_adversarial(oracle):
     m.close()
 
 
+def test_deflect_range_reduction_boundaries(oracle):
+    """Nodes close to PIEMD cores, where the atan and atanh arguments cross
+    their range-reduction thresholds (t^2 = 1, t^2 = 1/4) between
+    neighbouring rows, so that one node of a thread's pair takes the reduced
+    form and the other the polynomial: every node within its bound, in every
+    launch shape (paired, odd and single nodes), with identical values."""
+    rng = np.random.default_rng(77)
+    n = 12
+    p = np.zeros((8, n))
+    p[0] = W.PIEMD
+    p[1] = rng.uniform(-1.5, 1.5, n)
+    p[2] = rng.uniform(-1.5, 1.5, n)
+    p[3] = rng.uniform(0.05, 0.6, n)
+    p[4] = rng.uniform(0.0, np.pi, n)
+    p[5] = rng.uniform(0.03, 0.3, n)
+    p[6] = rng.uniform(20.0, 150.0, n)
+    p[7] = rng.uniform(150.0, 900.0, n)
+    grid = (-2.0, -1.9, 4.0 / 160, 3.8 / 153, 161, 154)
+    ref, _ = oracle.deflect_grid(p, grid, n_threads=4)
+    m = lt.Model(n, 1)
+    m.set_params(p[None])
+    first = None
+    for shape in range(m.num_shapes()):
+        m.set_shape(shape)
+        a, e = m.deflect_grid(grid, precision=lt.MIXED, with_error=True)
+        assert m.sync()[0] == lt.LT_OK
+        a, e = a.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
+        d = np.abs(a - ref).max(axis=-1)
+        assert np.all(np.isfinite(e)) and (d / e).max() <= 1.0, (shape, (d / e).max())
+        if first is None:
+            first = (a, e)
+        else:
+            np.testing.assert_array_equal(a, first[0])
+            np.testing.assert_array_equal(e, first[1])
+    m.close()
+
+
 @pytest.mark.parametrize("shape", range(8))
 def test_deflect_every_shape_within_bound(oracle, shape):
     """Every launch shape of the FP32 deflection on 300 potentials of all
