@@ -334,7 +334,7 @@ __host__ __device__ constexpr DeflectShape deflect_shape(int v) {
 // Work items of the FP32 triangle search.  A thread takes kSearch32Rows cells
 // of one cell column (a band); a sample's (band, cell column) positions,
 // band-major, are cut into items of kSearch32Threads positions.
-constexpr int kSearch32Threads = 128, kSearch32Rows = 2;
+constexpr int kSearch32Threads = 32, kSearch32Rows = 2;
 __host__ __device__ inline int64_t search32_items(int nx, int ny) {
   const int64_t cw = (int64_t)nx - 1, ch = (int64_t)ny - 1;
   if (cw <= 0 || ch <= 0) return 0;

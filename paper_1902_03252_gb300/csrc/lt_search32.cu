@@ -12,6 +12,7 @@ namespace lt {
 
 // ---------------------------------------------------------- triangle search
 constexpr int kSearchThreads = kSearch32Threads;  // positions per work item
+constexpr int kSearchBlocksPerSM = 16;
 constexpr int kMaxSrcSmem = 256;     // sources staged in shared memory at a time
 
 // Source data staged per sample: position relative coordinates use FP32.
@@ -207,7 +208,7 @@ __device__ __forceinline__ void emit_cell(const SampleGrid& g, int sample, int b
 // and barriers; its time barely changes between 1 and 20 sources): two cells
 // per thread halve the number of item iterations.  Four blocks per SM, with
 // the registers that allows, measure faster than five or six with spills.
-__global__ void __launch_bounds__(kSearchThreads, 4)
+__global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
                Hit* __restrict__ hits, int64_t hit_cap, Work64* __restrict__ work,
@@ -224,14 +225,18 @@ __global__ void __launch_bounds__(kSearchThreads, 4)
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   long long n_hit = 0, n_amb = 0, n_ref = 0;
   int staged = -1;  // sample whose whole source list is in ss (block-uniform)
-  int b = 0;        // sample of the previous item: the next one is usually in it
-  // static distribution of the items: the search follows the deflection on
-  // the same stream, so every block starts together and the fetch latency of
-  // a shared counter would sit on each item's critical path
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  // static distribution of the items, a contiguous range per block: the
+  // search follows the deflection on the same stream, so every block starts
+  // together, and the fetch latency of a shared counter would sit on each
+  // item's critical path; consecutive items mostly share a sample (its
+  // sources stay staged)
+  const int64_t per_block = (n_items + gridDim.x - 1) / gridDim.x;
+  const int64_t it0 = (int64_t)blockIdx.x * per_block;
+  const int64_t it1 = min(n_items, it0 + per_block);
+  int b = it0 < n_items ? find_sample(item_off, n_samples, it0) : 0;
+  for (int64_t item = it0; item < it1; ++item) {
     __syncthreads();  // the previous item's readers of sb / surv are done
-    if (n_samples > 1 && !(item_off[b] <= item && item < item_off[b + 1]))
-      b = find_sample(item_off, n_samples, item);
+    while (item >= item_off[b + 1]) ++b;
     const SampleGrid g = grids[b];
     const int sample = src.sample_base + b;
     // this thread's cell column i and cell rows j, j + 1 (see search32_items)
