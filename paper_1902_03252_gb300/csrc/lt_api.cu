@@ -362,7 +362,7 @@ lt_status ensure_resolve(lt_model* m) {
     LT_CUDA(cudaMalloc(&m->rs.keys, sizeof(unsigned long long) * cap));
     LT_CUDA(cudaMalloc(&m->rs.hval, sizeof(double2) * cap));
     LT_CUDA(cudaMalloc(&m->rs.ulist, sizeof(int32_t) * cap));
-    LT_CUDA(cudaMalloc(&m->rs.tval, sizeof(float4) * cap));
+    LT_CUDA(cudaMalloc(&m->rs.tval, sizeof(TightVal) * cap));
     LT_CUDA(cudaMalloc(&m->rs.flag64, sizeof(uint32_t) * cap));
     LT_CUDA(cudaMalloc(&m->rs.ulist64, sizeof(int32_t) * cap));
     // empty once here; every resolution leaves them empty again (k_res_tri)

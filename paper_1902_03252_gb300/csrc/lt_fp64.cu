@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kPrepThreads)
   Pot64* p64 = pot64 + (int64_t)b * n_pot;
   __shared__ int cnt[3];
   __shared__ int wcnt[3][NW];
-  __shared__ float qpart[NW], cpart[NW];
+  __shared__ float qpart[NW], cpart[NW], tpart[NW];
   if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < n_pot; k += kPrepThreads) {
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     atomicAdd(&cnt[kind], 1);
   }
   __syncthreads();
-  float qsum = 0.0f, csum = 0.0f;
+  float qsum = 0.0f, csum = 0.0f, tsum = 0.0f;
   int base[3] = {0, 0, 0};  // potentials of each kind in earlier chunks
   for (int k0 = 0; k0 < n_pot; k0 += kPrepThreads) {
     const int k = k0 + threadIdx.x;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     //    (Higham, Accuracy and Stability of Numerical Algorithms, Lemma 3.1).
     const double U = kU32d;
     auto gam = [U](double n) { return n * U >= 0.25 ? 1e30 : n / (1.0 - n * U); };
-    double Q, T, Gmax = 0.0;
+    double Q, T, Q2, Gmax = 0.0;
     if (kind == LT_SIS) {
       // Jacobian of b0 n(Delta): b0/|Delta| (2-norm).  Where |D| >= 2|e|:
       // error <= 2 b0 |e| / |D| with |e| <= u(1+u)(W2 + |Delta|), W2 =
@@ -188,6 +188,10 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[0] = make_float4(cx, cy, (float)p.b0, 0.f);
       f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
       Q = p.b0 * (gam(3.0 + kEpsRsqrt) + 3.0 * (1.0 + 3.0 * U));
+      // tight re-evaluation (node translated in FP64, rounded once: error
+      // u (1 + 2^-28) |Delta| per coordinate, so |e| <= 1.0001 u |Delta|):
+      // the Jacobian b0/|Delta| gives 1.01 u b0, with the evaluation terms
+      Q2 = p.b0 * (gam(3.0 + kEpsRsqrt) + 1.01);
       // |t_x| + |t_y| = g (|dx| + |dy|) <= sqrt(2) b0 (1 + (3 + eps_r) u)
       T = 1.41421357 * p.b0 * (1.0 + gam(5.0 + kEpsRsqrt) * U);
     } else if (kind == LT_SIE) {
@@ -211,6 +215,11 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[2] = make_float4((float)(p.b0 * r2 * p.c), (float)(p.b0 * r1 * p.s), 0.f, 0.f);
       f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
       Q = p.b0 * r2 * (gam(5.25 + kEpsRsqrt) + 16.04 * (1.0 + 3.0 * U) / r1);
+      // tight re-evaluation: translation error 1.0001 u |Delta|_1 and the
+      // rotation's 4.01 u |Delta|_1, so |e_z| <= sqrt(2) 5.02 u (1+3u) |Delta|_1
+      // <= 10.04 u (1+3u) |z| / r1, far below |z| / 2: 10.1 b0 r2 / r1 with
+      // the evaluation terms (r1 < 1e-3 is not bounded)
+      Q2 = r1 < 1e-3 ? 1e30 : p.b0 * r2 * (gam(5.25 + kEpsRsqrt) + 10.1 * (1.0 + 3.0 * U) / r1);
       // |t_x| + |t_y| <= sqrt(2) |rr (t1, t2)| <= sqrt(2) b0 r2 (1 + (6.25 + eps_r) u)
       T = 1.41421357 * p.b0 * r2 * (1.0 + gam(6.25 + kEpsRsqrt) * U);
     } else {
@@ -271,6 +280,12 @@ __global__ void __launch_bounds__(kPrepThreads)
       f.f[4] = make_float4(__double2float_ru(p0), __double2float_ru(Gx * Bs),
                            __double2float_ru(Gy * Bs), (float)(Bs * p.s));
       Q = 16.04 * (1.0 + 3.0 * U) * B / q;
+      // tight re-evaluation: the input errors are relative to the distance,
+      // |e'| <= sqrt(2) 5.02 u (1+3u) |Delta|_1 <= 10.04 u (1+3u) |Delta|, and
+      // psi_a >= q |Delta| along the segment (|e'| / psi_a <= 10.04 u / q is
+      // negligible for q >= 0.01), so B |H|_2 |e'| <= 10.1 (1+3u) u B / q; the
+      // evaluation terms stay per node (G)
+      Q2 = q < 0.01 ? 1e30 : 10.1 * (1.0 + 3.0 * U) * B / q;
       // coarse bound: the largest |gx|, |gy| over the plane.  |g_x| =
       // |atan(A) - atan(B)| <= atan(sig/q) (0 <= B <= A < sig/q) and |g_y| <=
       // atanh(sig) (the two atanh arguments lie in (-sig, sig) with one sign),
@@ -282,32 +297,37 @@ __global__ void __launch_bounds__(kPrepThreads)
       T = Bs * (fabs(p.c) + fabs(p.s)) * (mgx + mgy) * (1.0 + 2.0 * U);
     }
     qsum = __fadd_ru(qsum, __double2float_ru(Q));
+    tsum = __fadd_ru(tsum, __double2float_ru(Q2));
     // coarse bound: Q, the largest evaluation terms, and every accumulation
     // step's 2 (|PX| + |PY|) and flush's 2 (|AX| + |AY|) bounded by the
     // largest terms they can contain
     int w_partial, w_flush;
     sum_weights(rank, n_pot, cnt[LT_SIS], cnt[LT_PIEMD], &w_partial, &w_flush);
     csum = __fadd_ru(csum, __double2float_ru(Q + Gmax + 2.0 * T * (w_partial + w_flush)));
+    f.c64 = make_double2(p.cx, p.cy);
     pot32[(int64_t)b * n_pot + rank] = f;
   }
   // sum of the static bound terms (rounded up): fixed order (warp
   // butterflies, then warps)
   for (int o = 16; o > 0; o >>= 1) {
     qsum = __fadd_ru(qsum, __shfl_xor_sync(0xffffffffu, qsum, o));
+    tsum = __fadd_ru(tsum, __shfl_xor_sync(0xffffffffu, tsum, o));
     csum = __fadd_ru(csum, __shfl_xor_sync(0xffffffffu, csum, o));
   }
   if (lane == 0) {
     qpart[wid] = qsum;
+    tpart[wid] = tsum;
     cpart[wid] = csum;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float tot = 0.0f, ctot = 0.0f;
+    float tot = 0.0f, ctot = 0.0f, ttot = 0.0f;
     for (int w = 0; w < NW; ++w) {
       tot = __fadd_ru(tot, qpart[w]);
+      ttot = __fadd_ru(ttot, tpart[w]);
       ctot = __fadd_ru(ctot, cpart[w]);
     }
-    seg[b] = Seg32{cnt[LT_SIS], cnt[LT_PIEMD], cnt[LT_SIE], tot, ctot};
+    seg[b] = Seg32{cnt[LT_SIS], cnt[LT_PIEMD], cnt[LT_SIE], tot, ctot, ttot};
   }
 }
 

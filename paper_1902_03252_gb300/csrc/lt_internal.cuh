@@ -45,7 +45,8 @@ struct Pot64 {
 };
 static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 
-// FP32 record of one potential (5 float4 = 80 bytes), grouped by kind.
+// FP32 record of one potential (5 float4 and an FP64 centre = 96 bytes),
+// grouped by kind.
 //   SIS   : f[0] = {cx, cy, b0, 0}
 //   SIE   : f[0] = {cx, cy, r1 c, r1 s}; f[1] = {r2 c, r2 s, b0 r1 c, b0 r2 s};
 //           f[2] = {b0 r2 c, b0 r1 s, 0, 0} with r1,2 = sqrt(1 -+ eps)
@@ -60,10 +61,14 @@ static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 // coordinates are rounded once from FP64) becomes the coefficient P of the
 // per-node term P / distance (stage_p32); see k_prep for the derivation of
 // every coefficient.
+//   c64   : the centre in FP64 (cx, cy), read only by the tight FP32
+//           re-evaluation, which translates nodes in FP64; the deflection
+//           kernels stage f[0..4] alone.
 struct Pot32 {
   float4 f[5];
+  double2 c64;
 };
-static_assert(sizeof(Pot32) == 80, "Pot32 layout");
+static_assert(sizeof(Pot32) == 96, "Pot32 layout");
 
 // ------------------------------------------------ FP32 error-bound constants
 // Largest relative errors, in units of the FP32 unit roundoff u = 2^-24, of
@@ -100,12 +105,14 @@ __device__ __forceinline__ float node_bound(float terms, int n_pot) {
 }
 
 // Per-sample kind segments of the FP32 records (n_sis, n_piemd, n_sie), the
-// static part of the tight error bound, sum_k errQ_k, and the static part of
+// static part of the tight error bound, sum_k errQ_k, the static part of
 // the coarse one, which adds every potential's largest evaluation and
-// accumulation terms (units of u, rounded up).
+// accumulation terms, and that of the tight re-evaluation with FP64
+// translation (units of u, rounded up).
 struct Seg32 {
   int n_sis, n_piemd, n_sie;
   float q_tot, c_tot;
+  float q_tight;  // static terms of the tight re-evaluation's bound (k_res_tight32)
 };
 
 // Summation structure of the FP32 deflection: potentials are staged kChunk32
@@ -472,6 +479,14 @@ cudaError_t launch_search64(const double2* nodes, const SampleGrid* grids, const
 // (power of two) allocated, at least the smallest power of two >= 6 x
 // samples x work_cap of any chunk.  Every resolution leaves keys, flag64,
 // n_unique and n64 as it found them (all empty).
+// A node's deflection from the tight re-evaluation: the FP64 sum of its
+// potentials' FP32 deflections and a bound on both components' error.
+struct TightVal {
+  double ax, ay;
+  float e, pad;
+};
+static_assert(sizeof(TightVal) == 24, "TightVal layout");
+
 struct ResolveScratch {
   unsigned long long* keys;
   double2* hval;
@@ -479,7 +494,7 @@ struct ResolveScratch {
   int32_t* ulist;  // [cap]
   unsigned int* n_unique;
   unsigned long long cap;
-  float4* tval;      // [cap] tight FP32 (alpha_x, alpha_y, bound, 0) per slot
+  TightVal* tval;    // [cap] tight re-evaluation (alpha, bound) per slot
   uint32_t* flag64;  // [cap] 1 once a slot is listed for FP64
   int32_t* ulist64;  // [cap] slots to evaluate in FP64
   unsigned int* n64;

@@ -449,35 +449,40 @@ cudaError_t launch_search32(const float4* nodes, const SampleGrid* grids, const 
 // The search certifies with the coarse node bound.  The work items it leaves
 // undecided (and its certain hits whose position bound is too large) are
 // re-evaluated here before any FP64 work: every distinct node of those items
-// gets its FP32 deflection with the tight bound (k_res_tight32), and every
-// item is classified again with the search's own arithmetic (k_res_tri32).
-// Items decided there are done; the others list their nodes for the FP64
-// stage.
+// gets a tighter FP32 deflection (k_res_tight32), and every item is
+// classified again (k_res_tri32).  Items decided there are done; the others
+// list their nodes for the FP64 stage.
 //
-// k_res_tight32: one warp per node.  Lane l sums potentials l, l + 32, ...
-// (kind-sorted order) with the tight per-term and running-sum bound terms,
-// and the lanes' sums are combined by a butterfly of shuffles; every sum of
-// the butterfly is one rounding per component, charged |SX| + |SY|, and the
-// lanes' bound terms are summed along.  (IEEE addition is commutative, so
-// both lanes of a pair form the same sum and every lane ends with the same
-// total.)  The deflection differs from the deflection kernels' by the
-// summation order; the bound is that of this evaluation, which is the one
-// k_res_tri32 classifies with.
+// k_res_tight32: one block per node.  The node is translated to each
+// potential's centre in FP64 and rounded once (error u |Delta|, relative to
+// the distance, instead of the u (Theta + |c|) of an FP32 translation), the
+// potential's FP32 deflection is evaluated from there by the deflection
+// kernels' per-potential functions, and the potentials' deflections are
+// summed in FP64 (thread l takes potentials l, l + 128, ... of the
+// kind-sorted records; the threads' sums are combined by a butterfly of
+// shuffles per warp and then across the warps).  The
+// bound is then each potential's evaluation terms (G |g| per node for the
+// PIEMD, 2 |alpha_k|_1 for the rounding of the product that forms alpha_k)
+// plus the static input and evaluation terms Seg32::q_tight derived in
+// k_prep, plus the FP64 summation: at most n + 8 roundings of 2^-53 on
+// sum_k |alpha_k|_1 (summed in FP32, rounded up).
 constexpr int kTightThreads = 128;
 
 __global__ void __launch_bounds__(kTightThreads)
     k_res_tight32(const Pot32* __restrict__ pot32, const Seg32* __restrict__ seg, int n_pot,
                   const SampleGrid* __restrict__ grids, const unsigned long long* __restrict__ keys,
                   const int32_t* __restrict__ ulist, const unsigned int* __restrict__ n_unique,
-                  float4* __restrict__ tval, long long* counters) {
+                  TightVal* __restrict__ tval, long long* counters) {
+  constexpr int NW = kTightThreads / 32;
+  __shared__ double s_x[NW], s_y[NW];
+  __shared__ float s_a[NW], s_e[NW];
   grid_dependency_wait();
   const unsigned int nu = *n_unique;
   if (blockIdx.x == 0 && threadIdx.x == 0 && nu)
     atomicAdd((unsigned long long*)&counters[CNT_TIGHT_NODES], (unsigned long long)nu);
-  const int lane = threadIdx.x & 31;
-  const unsigned int warps = gridDim.x * (kTightThreads / 32);
-  for (unsigned int t = blockIdx.x * (kTightThreads / 32) + (threadIdx.x >> 5); t < nu;
-       t += warps) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // one block per node: thread l takes potentials l, l + 128, ...
+  for (unsigned int t = blockIdx.x; t < nu; t += gridDim.x) {
     const int32_t slot = ulist[t];
     const unsigned long long key = keys[slot];
     const int b = (int)(key >> 40);
@@ -485,30 +490,64 @@ __global__ void __launch_bounds__(kTightThreads)
     const SampleGrid g = grids[b];
     const Seg32 sg = seg[b];
     const int j = (int)(node / g.nx), i = (int)(node - (int64_t)j * g.nx);
-    // the node coordinates of the deflection kernels: rounded once from FP64
-    const float X = (float)(g.x0 + (double)i * g.dx);
-    const float Yv[1] = {(float)(g.y0 + (double)j * g.dy)};
+    // the node's FP64 position, formed as the FP64 stages and the reference
+    // form it (product and sum rounded separately, never contracted)
+    const double X = __dadd_rn(g.x0, __dmul_rn((double)i, g.dx));
+    const double Y = __dadd_rn(g.y0, __dmul_rn((double)j, g.dy));
     const Pot32* pb = pot32 + (int64_t)b * n_pot;
-    float PX[1] = {0.0f}, PY[1] = {0.0f}, ER[1] = {0.0f};
-    for (int k = lane; k < n_pot; k += 32) {
-      const Pot32 r = pb[k];
+    double sx = 0.0, sy = 0.0;
+    float er = 0.0f, sa = 0.0f;
+    for (int k = threadIdx.x; k < n_pot; k += kTightThreads) {
+      Pot32 r = pb[k];
+      // translated in FP64, rounded once; the record's centre set to 0 so
+      // that the function's own translation is exact
+      const float dx = (float)(X - r.c64.x);
+      const float dy[1] = {(float)(Y - r.c64.y)};
+      r.f[0].x = 0.0f;
+      r.f[0].y = 0.0f;
+      // the input errors are in q_tight; 1e-30 keeps an SIS/SIE node whose
+      // translation rounds to zero distance unbounded (+inf)
+      float px[1] = {0.0f}, py[1] = {0.0f}, ek[1] = {0.0f};
       if (k < sg.n_sis)
-        sis32_nodes<float, 1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
+        sis32_nodes<float, 1, true>(r.f, 1e-30f, dx, dy, px, py, ek);
       else if (k < sg.n_sis + sg.n_piemd)
-        piemd32_nodes<float, 1, true>(r.f, stage_p32(r, true, g.theta_max), X, Yv, PX, PY, ER);
+        piemd32_nodes<float, 1, true>(r.f, 1e-30f, dx, dy, px, py, ek);
       else
-        sie32_nodes<float, 1, true>(r.f, stage_p32(r, false, g.theta_max), X, Yv, PX, PY, ER);
+        sie32_nodes<float, 1, true>(r.f, 1e-30f, dx, dy, px, py, ek);
+      sx += (double)px[0];
+      sy += (double)py[0];
+      sa = __fadd_ru(sa, __fadd_ru(fabsf(px[0]), fabsf(py[0])));
+      er += ek[0];
     }
-    float sx = PX[0], sy = PY[0], er = ER[0];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
       sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sa = __fadd_ru(sa, __shfl_xor_sync(0xffffffffu, sa, o));
       er += __shfl_xor_sync(0xffffffffu, er, o);
-      er += fabsf(sx) + fabsf(sy);
     }
-    if (lane == 0)
-      tval[slot] = make_float4(sx, sy, node_bound(__fadd_ru(er, sg.q_tot), n_pot), 0.0f);
+    if (lane == 0) {
+      s_x[wid] = sx;
+      s_y[wid] = sy;
+      s_a[wid] = sa;
+      s_e[wid] = er;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < NW; ++w) {
+        sx += s_x[w];
+        sy += s_y[w];
+        sa = __fadd_ru(sa, s_a[w]);
+        er += s_e[w];
+      }
+      // FP64 summation of n terms (sequential per thread, 5 butterfly
+      // levels, NW - 1 additions across warps): at most n + 8 roundings of
+      // 2^-53 each on sum |alpha_k|, in units of u: (n + 8) 2^-29 sa
+      const float fp64sum = __fmul_ru(sa, __fmul_ru((float)(n_pot + 8), 1.8626451e-09f));
+      const float e = node_bound(__fadd_ru(__fadd_ru(er, sg.q_tight), fp64sum), n_pot);
+      tval[slot] = TightVal{sx, sy, e, 0.0f};
+    }
+    __syncthreads();  // the block's partial sums are read before the next node
   }
 }
 
@@ -524,7 +563,7 @@ __device__ __forceinline__ void tri_vertex32(int nx, int64_t tri, int v, int& i,
 __global__ void k_res_tri32(const SampleGrid* __restrict__ grids, Sources src,
                             Work64* __restrict__ work, const unsigned long long* __restrict__ work_count,
                             int n_samples, int64_t work_cap, const int32_t* __restrict__ vslot,
-                            const float4* __restrict__ tval, Hit* __restrict__ hits,
+                            const TightVal* __restrict__ tval, Hit* __restrict__ hits,
                             int64_t hit_cap, unsigned long long* hit_count, long long* counters,
                             uint32_t* status, uint32_t* __restrict__ flag64,
                             int32_t* __restrict__ ulist64, unsigned int* __restrict__ n64) {
@@ -540,11 +579,18 @@ __global__ void k_res_tri32(const SampleGrid* __restrict__ grids, Sources src,
     if ((unsigned long long)idx >= (cnt < (unsigned long long)work_cap ? cnt : work_cap)) continue;
     const Work64 wk = work[f];
     const SampleGrid g = grids[b];
-    // the source as the search stages it
+    // the mapped vertex relative to the source, beta_v - P = (theta_v - P)
+    // - r alpha_v, formed in FP64 from the node's FP64 position, the FP64
+    // source and ratio and the re-evaluated deflection (every FP64 operation
+    // rounded separately), then rounded once to FP32 for the orientation
+    // test.  Its bound: r E (the deflection's) + the rounding to FP32,
+    // u |.|_1, + the three FP64 roundings of each coordinate (2^-50 on the
+    // magnitudes involved, a margin over 3 x 2^-53), and the second-order
+    // terms (mu_up).
     const double* sxy = src.xy + (int64_t)wk.sample * src.n_src * 2;
-    const float px = (float)sxy[2 * wk.src], py = (float)sxy[2 * wk.src + 1];
-    const float r = (float)src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
-    const float mu0 = __fmul_ru(u, __fmaf_ru(4.0f, g.theta_max, __fadd_ru(fabsf(px), fabsf(py))));
+    const double px = sxy[2 * wk.src], py = sxy[2 * wk.src + 1];
+    const double r = src.r[(int64_t)wk.sample * src.n_src * (src.stride_r ? 1 : 0) + wk.src];
+    const float rf = __double2float_ru(fabs(r));
     float ax[3], ay[3], mv[3];
     bool ok = true;
     for (int v = 0; v < 3; ++v) {
@@ -552,17 +598,16 @@ __global__ void k_res_tri32(const SampleGrid* __restrict__ grids, Sources src,
       if (slot < 0) { ok = false; break; }
       int i, j;
       tri_vertex32(g.nx, wk.tri, v, i, j);
-      const float4 a = tval[slot];
-      // relative mapped vertex and its bound, exactly as in the search
-      const float dx = fmaf((float)i, g.dxf, g.x0f) - px;
-      const float dy = fmaf((float)j, g.dyf, g.y0f) - py;
-      ax[v] = fmaf(-r, a.x, dx);
-      ay[v] = fmaf(-r, a.y, dy);
+      const TightVal a = tval[slot];
+      const double dx = __dsub_rn(__dadd_rn(g.x0, __dmul_rn((double)i, g.dx)), px);
+      const double dy = __dsub_rn(__dadd_rn(g.y0, __dmul_rn((double)j, g.dy)), py);
+      const double bx = __dsub_rn(dx, __dmul_rn(r, a.ax)), by = __dsub_rn(dy, __dmul_rn(r, a.ay));
+      ax[v] = (float)bx;
+      ay[v] = (float)by;
+      const float mag = __double2float_ru(fabs(dx) + fabs(dy) + fabs(r) * (fabs(a.ax) + fabs(a.ay)));
       mv[v] = mu_up(__fmaf_ru(
-          r, a.z,
-          __fmaf_ru(u * 2.0f, __fmaf_ru(r, __fadd_ru(fabsf(a.x), fabsf(a.y)),
-                                        __fadd_ru(fabsf(dx), fabsf(dy))),
-                    mu0)));
+          rf, a.e,
+          __fmaf_ru(u, __fadd_ru(fabsf(ax[v]), fabsf(ay[v])), __fmul_ru(8.8817842e-16f, mag))));
     }
     if (!ok) {  // cannot happen with the table sized as it is; recorded, never silent
       atomicOr(status, ST_OVERFLOW_WORK);
@@ -617,8 +662,8 @@ cudaError_t launch_tight32(const Pot32* pot32, const Seg32* seg, int n_pot,
                            Hit* hits, int64_t hit_cap, unsigned long long* hit_count,
                            long long* counters, uint32_t* status, ResolveScratch rs,
                            int sm_count, cudaStream_t st) {
-  // one warp per distinct node (at most three per item)
-  int64_t b1 = ((int64_t)n_samples * work_cap * 3 * 32 + kTightThreads - 1) / kTightThreads;
+  // one block per distinct node (at most three per item)
+  int64_t b1 = (int64_t)n_samples * work_cap * 3;
   if (b1 > (int64_t)sm_count * 8) b1 = (int64_t)sm_count * 8;
   cudaError_t e = launch_pdl(k_res_tight32, dim3((unsigned)b1), dim3(kTightThreads), st, pot32,
                              seg, n_pot, grids, rs.keys, rs.ulist, rs.n_unique, rs.tval, counters);
