@@ -291,7 +291,7 @@ lt_status lt_profile_stages(lt_model* model, uint32_t mask);
  * LT_ERR_NONFINITE (invalid parameters, which are neutralised to zero mass).
  * Returns LT_ERR_INVALID_ARG for null pointers, a bad grid or n_pot outside
  * [1, 4096]; LT_ERR_CUDA if a runtime call fails.
- * Its scratch is a fixed file-scope device array of about 0.8 MiB that every
+ * Its scratch is a fixed file-scope device array of about 0.9 MiB that every
  * GPU loading the library holds until exit; the call itself allocates
  * nothing.  The first call on a device resolves that array's address
  * (cudaGetSymbolAddress, with the device current).  Under CUDA's lazy module
