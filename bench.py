@@ -603,6 +603,18 @@ def _time(fn, torch, steps):
     return e0.elapsed_time(e1) / steps / 1e3
 
 
+def _deflect_rate(m, call, torch, npot):
+    """node x potential / s of the FP32 deflection kernel alone inside one
+    profiled call (CUDA events around each deflection launch, untimed run)."""
+    m.profile(True, stages=["deflect"])
+    m.profile_read(reset=True)
+    call()
+    torch.cuda.synchronize()
+    d = m.profile_read(reset=True)["deflect"]
+    m.profile(False)
+    return npot / (d["ms"] * 1e-3) if d["ms"] > 0 else None
+
+
 def extra_latency(lt, W, torch, dev, steps=200):
     """The single-SIS case (256^2 nodes): time per chi^2, device-timed and as
     the host sees it (parameters in, chi^2 back, waiting for each result)."""
@@ -689,6 +701,9 @@ def extra_batched(lt, W, torch, dev, peak, rank, world, max_over_ranks, barrier,
     t = max_over_ranks(t)
     chi2 = sharding.gather_in_order(out.cpu().tolist(), mine, w.batch)
     npot = w.node_pot()
+    npot_mine = sum(w.grids[b].nodes for b in mine) * w.n_pot
+    krate = _deflect_rate(m, lambda: m.chi2(grids, obs, precision=lt.MIXED, out=out), torch,
+                          npot_mine)
     m.close()
     return {"workload": "c3: 1024 samples x 50 PIEMD, grids 500^2..2000^2, 10 systems",
             "ranks": world, "samples_per_rank": [len(s) for s in
@@ -698,6 +713,10 @@ def extra_batched(lt, W, torch, dev, peak, rank, world, max_over_ranks, barrier,
             # the whole batch (search, FP64 resolution, matching included)
             # against the deflection's roofline (per GPU)
             "frac_of_deflection_roofline": npot / t / (peak * world),
+            # the deflection kernel alone inside the batch (rank 0's shard), and
+            # the whole batch's rate over it: what the other stages cost
+            "deflect_kernel_node_pot_per_s": krate,
+            "batch_over_deflect_kernel": (npot_mine / (t * 1.0)) / krate if krate else None,
             "chi2_gathered": len(chi2), "chi2_sum": float(sum(chi2)),
             "status": int(st), "stats": stats}
 
@@ -734,14 +753,17 @@ def extra_large(lt, W, torch, dev, peak, steps=2):
     t_val = _time(lambda: m.chi2(grids, obs, precision=lt.MIXED), torch, steps)
     t_grad = _time(lambda: m.chi2_grad(grids, obs, precision=lt.MIXED), torch, steps)
     st, stats = m.sync()
-    m.close()
     npot = w.node_pot()
+    krate = _deflect_rate(m, lambda: m.chi2(grids, obs, precision=lt.MIXED), torch, npot)
+    m.close()
     return {"workload": "c5: 64 samples x 1000 PIEMD, 4000^2 grids, 100 systems, chi^2 and "
                         "gradients per call", "batch": w.batch,
             "chi2_s_per_batch": t_val, "chi2_grad_s_per_batch": t_grad,
             "chi2_evals_per_s": w.batch / t_val, "chi2_grad_evals_per_s": w.batch / t_grad,
             "deflect_shape": shape, "node_pot_per_s": npot / t_val,
             "frac_of_deflection_roofline": npot / t_val / peak,
+            "deflect_kernel_node_pot_per_s": krate,
+            "batch_over_deflect_kernel": (npot / t_val) / krate if krate else None,
             "status": int(st), "stats": stats}
 
 

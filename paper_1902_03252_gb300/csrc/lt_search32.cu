@@ -136,7 +136,6 @@ __device__ __forceinline__ float mu_up(float m) { return __fmul_ru(m, 1.00000048
 
 struct StripBox {
   float tx0, tx1, ty0, ty1, ax0, ax1, ay0, ay1, e, l;
-  int any, pad;
 };
 
 // Image position of an FP32-certified hit, interpolated in FP64 from the
@@ -215,14 +214,11 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
                int64_t work_cap, unsigned long long* hit_count, unsigned long long* work_count,
                long long* counters, uint32_t* status,
                unsigned long long* __restrict__ /*next_item: unused, static items*/) {
-  constexpr int kStrips = kSearchThreads / 32;
   static_assert(kSearch32Rows == 2, "the kernel handles two cell rows per thread");
+  static_assert(kSearchThreads == 32, "one warp per block and per work item");
   __shared__ SrcSmem ss[kMaxSrcSmem];
-  __shared__ StripBox sb[kStrips];
-  __shared__ unsigned short surv[kStrips][kMaxSrcSmem];
-  __shared__ int n_surv[kStrips];
   const float u = kU32;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x;
   long long n_hit = 0, n_amb = 0, n_ref = 0;
   int staged = -1;  // sample whose whole source list is in ss (block-uniform)
   // static distribution of the items, a contiguous range per block: the
@@ -235,7 +231,6 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
   const int64_t it1 = min(n_items, it0 + per_block);
   int b = it0 < n_items ? find_sample(item_off, n_samples, it0) : 0;
   for (int64_t item = it0; item < it1; ++item) {
-    __syncthreads();  // the previous item's readers of sb / surv are done
     while (item >= item_off[b + 1]) ++b;
     const SampleGrid g = grids[b];
     const int sample = src.sample_base + b;
@@ -276,72 +271,71 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
         fmaxf(fmaxf(fmaxf(fabsf(v00.x) + fabsf(v00.y), fabsf(v10.x) + fabsf(v10.y)),
                     fmaxf(fabsf(v01.x) + fabsf(v01.y), fabsf(v11.x) + fabsf(v11.y))),
               fmaxf(fabsf(v02.x) + fabsf(v02.y), fabsf(v12.x) + fabsf(v12.y)));
-    {
-      const float inf = __int_as_float(0x7f800000);
-      StripBox box;
-      box.tx0 = warp_min(validA ? xl : inf);
-      box.tx1 = warp_max(validA ? xr : -inf);
-      box.ty0 = warp_min(validA ? yb : inf);
-      box.ty1 = warp_max(validA ? (validB ? yt : ym) : -inf);
-      box.ax0 = warp_min(validA ? fminf(fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)),
-                                        fminf(v02.x, v12.x))
-                                : inf);
-      box.ax1 = warp_max(validA ? fmaxf(fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)),
-                                        fmaxf(v02.x, v12.x))
-                                : -inf);
-      box.ay0 = warp_min(validA ? fminf(fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)),
-                                        fminf(v02.y, v12.y))
-                                : inf);
-      box.ay1 = warp_max(validA ? fmaxf(fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)),
-                                        fmaxf(v02.y, v12.y))
-                                : -inf);
-      box.e = warp_max(validA ? emax : 0.0f);
-      box.l = warp_max(validA ? lmax : 0.0f);
-      box.any = __any_sync(0xffffffffu, validA) ? 1 : 0;
-      box.pad = 0;
-      if (lane == 0) sb[wid] = box;
-    }
+    // the strip's box (every lane receives the warp-wide minima and maxima)
+    const float inf = __int_as_float(0x7f800000);
+    StripBox B;
+    B.tx0 = warp_min(validA ? xl : inf);
+    B.tx1 = warp_max(validA ? xr : -inf);
+    B.ty0 = warp_min(validA ? yb : inf);
+    B.ty1 = warp_max(validA ? (validB ? yt : ym) : -inf);
+    B.ax0 = warp_min(validA ? fminf(fminf(fminf(v00.x, v10.x), fminf(v01.x, v11.x)),
+                                    fminf(v02.x, v12.x))
+                            : inf);
+    B.ax1 = warp_max(validA ? fmaxf(fmaxf(fmaxf(v00.x, v10.x), fmaxf(v01.x, v11.x)),
+                                    fmaxf(v02.x, v12.x))
+                            : -inf);
+    B.ay0 = warp_min(validA ? fminf(fminf(fminf(v00.y, v10.y), fminf(v01.y, v11.y)),
+                                    fminf(v02.y, v12.y))
+                            : inf);
+    B.ay1 = warp_max(validA ? fmaxf(fmaxf(fmaxf(v00.y, v10.y), fmaxf(v01.y, v11.y)),
+                                    fmaxf(v02.y, v12.y))
+                            : -inf);
+    B.e = warp_max(validA ? emax : 0.0f);
+    B.l = warp_max(validA ? lmax : 0.0f);
+    const bool any_valid = __any_sync(0xffffffffu, validA);
+    // |box corners|_1, the same for every source of the strip
+    const float box1 = __fadd_ru(__fadd_ru(fabsf(B.tx0), fabsf(B.tx1)),
+                                 __fadd_ru(fabsf(B.ty0), fabsf(B.ty1)));
     const double* sxy = src.xy + (int64_t)sample * src.n_src * 2;
     const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
     for (int s0 = 0; s0 < src.n_src; s0 += kMaxSrcSmem) {
       const int sn = min(kMaxSrcSmem, src.n_src - s0);
       const bool whole = sn == src.n_src;
-      if (!whole) __syncthreads();  // earlier chunk's readers of ss are done
       if (!whole || staged != sample) {
-        for (int v = threadIdx.x; v < sn; v += kSearchThreads) {
+        __syncwarp();  // earlier readers of ss are done
+        for (int v = lane; v < sn; v += kSearchThreads) {
           const float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
           ss[v] = SrcSmem{px, py, (float)sr[s0 + v],
                           __fmul_ru(u, __fmaf_ru(4.0f, g.theta_max,
                                                  __fadd_ru(fabsf(px), fabsf(py))))};
         }
+        __syncwarp();
       }
       staged = whole ? sample : -1;
-      if (threadIdx.x < kStrips) n_surv[threadIdx.x] = 0;
-      __syncthreads();
-      // (1) one thread per (strip, source) pair
-      for (int pidx = threadIdx.x; pidx < kStrips * sn; pidx += kSearchThreads) {
-        const int w = pidx % kStrips, k = pidx / kStrips;
-        const StripBox B = sb[w];
-        const SrcSmem S = ss[k];
-        const float wmu = mu_up(__fmaf_ru(
-            S.r, B.e,
-            __fmaf_ru(u, __fmaf_ru(2.0f,
-                                   __fadd_ru(__fadd_ru(__fadd_ru(fabsf(B.tx0), fabsf(B.tx1)),
-                                                       __fadd_ru(fabsf(B.ty0), fabsf(B.ty1))),
-                                             __fadd_ru(fabsf(S.px), fabsf(S.py))),
-                                   __fmul_ru(__fmul_ru(4.0f, S.r), B.l)),
-                      S.mu0)));
-        const float bx0 = fmaf(-S.r, B.ax1, B.tx0), bx1 = fmaf(-S.r, B.ax0, B.tx1);
-        const float by0 = fmaf(-S.r, B.ay1, B.ty0), by1 = fmaf(-S.r, B.ay0, B.ty1);
-        const bool keep = B.any && S.px >= bx0 - wmu && S.px <= bx1 + wmu &&
-                          S.py >= by0 - wmu && S.py <= by1 + wmu;
-        if (keep) surv[w][atomicAdd(&n_surv[w], 1)] = (unsigned short)k;
-      }
-      __syncthreads();
-      // (2) each warp: its strip's surviving sources, one per iteration
-      const int ns = n_surv[wid];
-      for (int q = 0; q < ns; ++q) {
-        const int k = surv[wid][q];
+      for (int c0 = 0; c0 < sn; c0 += 32) {
+        // (1) lane k tests source c0 + k against the strip's box; the warp
+        // then walks the surviving sources (a ballot mask), one at a time
+        unsigned keep_mask = 0u;
+        if (any_valid) {
+          bool keep = false;
+          if (c0 + lane < sn) {
+            const SrcSmem S = ss[c0 + lane];
+            const float wmu = mu_up(__fmaf_ru(
+                S.r, B.e,
+                __fmaf_ru(u, __fmaf_ru(2.0f, __fadd_ru(box1, __fadd_ru(fabsf(S.px), fabsf(S.py))),
+                                       __fmul_ru(__fmul_ru(4.0f, S.r), B.l)),
+                          S.mu0)));
+            const float bx0 = fmaf(-S.r, B.ax1, B.tx0), bx1 = fmaf(-S.r, B.ax0, B.tx1);
+            const float by0 = fmaf(-S.r, B.ay1, B.ty0), by1 = fmaf(-S.r, B.ay0, B.ty1);
+            keep = S.px >= bx0 - wmu && S.px <= bx1 + wmu && S.py >= by0 - wmu &&
+                   S.py <= by1 + wmu;
+          }
+          keep_mask = __ballot_sync(0xffffffffu, keep);
+        }
+      // (2) the surviving sources, one per iteration
+      while (keep_mask) {
+        const int k = c0 + __ffs(keep_mask) - 1;
+        keep_mask &= keep_mask - 1u;
         const SrcSmem S = ss[k];
         const float dl = xl - S.px, dr = xr - S.px;
         const float db = yb - S.py, dm = ym - S.py, dt = yt - S.py;
@@ -410,6 +404,7 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
         n_hit += (int)ok0 + (int)ok1;
         n_amb += (int)(r0 == 2) + (int)(r1 == 2);
         n_ref += (int)(r0 == 1 && !ok0) + (int)(r1 == 1 && !ok1);
+      }
       }
     }
   }
