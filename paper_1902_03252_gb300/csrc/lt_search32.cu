@@ -192,21 +192,21 @@ __device__ __forceinline__ void emit_cell(const SampleGrid& g, int sample, int b
                    work_count + b, status, counters);
 }
 
-// One work item = 128 positions, 4 warps of 32 ("strips"); a position is two
-// vertically adjacent cells of one cell column (rows j and j + 1), which
-// share a row of nodes.  For each chunk of sources: (1) every (strip, source)
-// pair is tested once, by one thread, against a conservative source-plane box
-// of the strip,
+// One work item = 32 positions ("a strip"), one warp, one block; a position
+// is two vertically adjacent cells of one cell column (rows j and j + 1),
+// which share a row of nodes.  For each chunk of up to 32 sources: (1) lane k
+// tests source k against a conservative source-plane box of the strip,
 //   beta_x in [min theta_x - r max alpha_x, max theta_x - r min alpha_x]
-// (the same in y) widened by the strip's largest vertex uncertainty; the
-// surviving sources of each strip are compacted into a shared list; (2) each
-// warp runs the per-cell test only for its strip's survivors.  Most pairs
-// never reach the per-cell arithmetic.
+// (the same in y) widened by the strip's largest vertex uncertainty, whose
+// extremes every lane receives from the warp reductions; (2) the warp walks
+// the surviving sources (a ballot mask) and runs the per-cell test for each.
+// Most pairs never reach the per-cell arithmetic.  No barrier and no shared
+// memory besides the staged sources.
 //
-// The kernel is latency-bound (the per-item chain of loads, warp reductions
-// and barriers; its time barely changes between 1 and 20 sources): two cells
-// per thread halve the number of item iterations.  Four blocks per SM, with
-// the registers that allows, measure faster than five or six with spills.
+// The kernel is latency-bound (the per-item chain of node loads and warp
+// reductions; its time barely changes between 1 and 20 sources): two cells
+// per thread halve the number of item iterations.  Sixteen one-warp blocks
+// per SM (128 registers) measure faster than more blocks with spills.
 __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
     k_search32(const float4* __restrict__ nodes, const SampleGrid* __restrict__ grids,
                const int64_t* __restrict__ item_off, int n_samples, int64_t n_items, Sources src,
