@@ -14,12 +14,15 @@
 // every observed image of the system, coefficient -(r/n) sum lambda) of
 // coefficient . d alpha_k(point) / d p_k.
 //
-//   k_adj_hits / k_adj_bary  build those points and coefficients (vertex
-//                deflections of matched triangles recomputed in FP64);
-//   k_adj_grad   one warp per potential: the 2x6 Jacobian of its deflection
+//   k_adj_vtx / k_adj_lam  build those points and coefficients (vertex
+//                deflections of matched triangles recomputed in FP64, one
+//                block per vertex; then one block per sample for the
+//                coefficients);
+//   k_adj_grad   one block per potential: the 2x6 Jacobian of its deflection
 //                w.r.t. (x, y, e, phi, r_core, sigma_v) at every point, in
-//                FP32, contracted with the coefficients (one point per lane);
-//                FP32 warp sums of 32 points are accumulated in FP64.
+//                FP32, contracted with the coefficients (one point per lane,
+//                the warps over the point chunks); FP32 warp sums of 32
+//                points are accumulated in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,100 +34,130 @@ namespace lt {
 constexpr int kAdjThreads = 128;
 
 // ------------------------------------------------------------ coefficients
-// Pass 1, one block per (sample, observed image m): if m is the first observed
-// image matched to its predicted image h, build h's three vertex points.  The
-// vertex deflections are recomputed in FP64 (threads split the potentials,
-// sums in index order): M = [beta_B - beta_A, beta_C - beta_A] is a
-// difference of large deflections and its FP32 rounding would be amplified
-// by M's conditioning in magnified triangles.
-constexpr int kAdjHitThreads = 384;  // one group of 128 per triangle vertex
+// Pass 1a, one block per (sample, observed image m, vertex v): if m is the
+// first observed image matched to its predicted image h, the FP64
+// deflection of vertex v of h's triangle (threads split the potentials, sums
+// in index order), parked in the point's coefficient fields for pass 1b.
+// The vertex deflections are recomputed in FP64: M = [beta_B - beta_A,
+// beta_C - beta_A] is a difference of large deflections and its FP32 rounding
+// would be amplified by M's conditioning in magnified triangles.  One block
+// per vertex spreads a model's matched triangles over three times as many
+// SMs as one block per triangle.
+constexpr int kAdjVtxThreads = 128;
 
-__global__ void __launch_bounds__(kAdjHitThreads)
-    k_adj_hits(const Pot64* __restrict__ pot64, int n_pot, int batch,
-               const SampleGrid* __restrict__ grids, const Hit* __restrict__ hits,
-               int64_t hit_cap, lt_obs obs, const int32_t* __restrict__ match_hit,
-               double2* __restrict__ lam, AdjPt* __restrict__ pts, int P) {
-  __shared__ double2 buf[kAdjHitThreads];
-  __shared__ double res[6];
-  for (int64_t f = blockIdx.x; f < (int64_t)batch * obs.n_obs; f += gridDim.x) {
+// h's owner: the first observed image of the sample matched to it
+__device__ __forceinline__ bool adj_owner(const int32_t* mh, int m, int h) {
+  bool owner = h >= 0;
+  for (int k = 0; k < m && owner; ++k) owner = mh[k] != h;
+  return owner;
+}
+
+// triangle vertices of hit H: T0 = (00, 10, 11), T1 = (00, 11, 01)
+__device__ __forceinline__ void adj_vertex(const SampleGrid& g, int64_t tri, int v, double& X,
+                                           double& Y) {
+  const int64_t cell = tri / 2;
+  const int t = (int)(tri % 2);
+  const int i = (int)(cell % (g.nx - 1)), j = (int)(cell / (g.nx - 1));
+  const int di = v == 0 ? 0 : (v == 1 ? 1 : (t == 0 ? 1 : 0));
+  const int dj = v == 0 ? 0 : (v == 1 ? (t == 0 ? 0 : 1) : 1);
+  X = g.x0 + (double)(i + di) * g.dx;
+  Y = g.y0 + (double)(j + dj) * g.dy;
+}
+
+__global__ void __launch_bounds__(kAdjVtxThreads)
+    k_adj_vtx(const Pot64* __restrict__ pot64, int n_pot, int batch,
+              const SampleGrid* __restrict__ grids, const Hit* __restrict__ hits,
+              int64_t hit_cap, lt_obs obs, const int32_t* __restrict__ match_hit,
+              AdjPt* __restrict__ pts, int P) {
+  __shared__ double2 buf[kAdjVtxThreads];
+  __shared__ double res[2];
+  for (int64_t f3 = blockIdx.x; f3 < (int64_t)batch * obs.n_obs * 3; f3 += gridDim.x) {
+    const int64_t f = f3 / 3;
+    const int v = (int)(f3 - f * 3);
     const int b = (int)(f / obs.n_obs);
     const int m = (int)(f - (int64_t)b * obs.n_obs);
     const int32_t* mh = match_hit + (int64_t)b * obs.n_obs;
-    AdjPt* pp = pts + (int64_t)b * P;
     const int h = mh[m];
-    bool owner = h >= 0;
-    for (int k = 0; k < m && owner; ++k) owner = mh[k] != h;
-    if (!owner) {  // block-uniform
-      if (threadIdx.x < 3) pp[3 * m + threadIdx.x] = AdjPt{0.0, 0.0, 0.0, 0.0};
-      if (threadIdx.x == 0) lam[f] = make_double2(0.0, 0.0);
-      continue;
-    }
+    if (!adj_owner(mh, m, h)) continue;  // block-uniform
     const SampleGrid g = grids[b];
     const Hit H = hits[(int64_t)b * hit_cap + h];
-    // triangle vertices: T0 = (00, 10, 11), T1 = (00, 11, 01)
-    const int64_t cell = H.tri / 2;
-    const int t = (int)(H.tri % 2);
-    const int i = (int)(cell % (g.nx - 1)), j = (int)(cell / (g.nx - 1));
-    const int di[3] = {0, 1, t == 0 ? 1 : 0};
-    const int dj[3] = {0, t == 0 ? 0 : 1, 1};
-    double TX[3], TY[3];
-    for (int v = 0; v < 3; ++v) {
-      TX[v] = g.x0 + (double)(i + di[v]) * g.dx;
-      TY[v] = g.y0 + (double)(j + dj[v]) * g.dy;
-    }
-    block_alpha64<kAdjHitThreads>(pot64 + (int64_t)b * n_pot, n_pot, 3, TX, TY, &res[0],
-                                  &res[3], buf);
-    if (threadIdx.x == 0) {
-      // dchi^2/dx of this predicted image, over every observed image matched to it
-      double Gx = 0.0, Gy = 0.0;
-      for (int k = m; k < obs.n_obs; ++k) {
-        if (mh[k] != h) continue;
-        const double s2 = obs.sigma[k] * obs.sigma[k];
-        Gx += -2.0 * (obs.x[k] - H.x) / s2;
-        Gy += -2.0 * (obs.y[k] - H.y) / s2;
-      }
-      const double r = obs.dls_ds[obs.sys[m]];
-      double BX[3], BY[3];
-      for (int v = 0; v < 3; ++v) {
-        BX[v] = TX[v] - r * res[v];
-        BY[v] = TY[v] - r * res[3 + v];
-      }
-      const double M00 = BX[1] - BX[0], M01 = BX[2] - BX[0];
-      const double M10 = BY[1] - BY[0], M11 = BY[2] - BY[0];
-      const double det = M00 * M11 - M01 * M10;
-      const double dB = Gx * (TX[1] - TX[0]) + Gy * (TY[1] - TY[0]);
-      const double dC = Gx * (TX[2] - TX[0]) + Gy * (TY[2] - TY[0]);
-      // lambda = M^-T (dB, dC)
-      const double lx = (M11 * dB - M10 * dC) / det;
-      const double ly = (-M01 * dB + M00 * dC) / det;
-      lam[f] = make_double2(lx, ly);
-      for (int v = 0; v < 3; ++v)
-        pp[3 * m + v] = AdjPt{TX[v], TY[v], r * H.w[v] * lx, r * H.w[v] * ly};
-    }
-    __syncthreads();
+    double TX, TY;
+    adj_vertex(g, H.tri, v, TX, TY);
+    block_alpha64<kAdjVtxThreads>(pot64 + (int64_t)b * n_pot, n_pot, 1, &TX, &TY, &res[0],
+                                  &res[1], buf);
+    if (threadIdx.x == 0) pts[(int64_t)b * P + 3 * m + v] = AdjPt{TX, TY, res[0], res[1]};
+    __syncthreads();  // res is read before the next vertex overwrites it
   }
 }
 
-// Pass 2: every observed image of system i is a barycentre point with
-// coefficient -(r_i / n_i) sum over the system's predicted images of lambda.
-__global__ void k_adj_bary(int batch, lt_obs obs, const double2* __restrict__ lam,
-                           AdjPt* __restrict__ pts, int P) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= (int64_t)batch * obs.n_obs) return;
-  const int b = (int)(f / obs.n_obs);
-  const int m = (int)(f - (int64_t)b * obs.n_obs);
-  const int i = obs.sys[m];
-  const double2* lb = lam + (int64_t)b * obs.n_obs;
-  double Lx = 0.0, Ly = 0.0;
-  int n = 0;
-  for (int k = 0; k < obs.n_obs; ++k) {
-    if (obs.sys[k] != i) continue;
-    ++n;
-    Lx += lb[k].x;
-    Ly += lb[k].y;
+// Pass 1b, one block per sample, threads over its observed images m: for
+// h's owner, the coefficients of its three vertex points from the parked
+// deflections: lambda = M^-T (dB, dC) with (dB, dC) the chi^2 gradient of
+// h's position along the triangle's image-plane edges; other images get zero
+// points.  Pass 2, after a block barrier: every observed image of system i is
+// a barycentre point with coefficient -(r_i / n_i) sum over the system's
+// predicted images of lambda.
+constexpr int kAdjLamThreads = 256;
+
+__global__ void __launch_bounds__(kAdjLamThreads)
+    k_adj_lam(int batch, const Hit* __restrict__ hits, int64_t hit_cap, lt_obs obs,
+              const int32_t* __restrict__ match_hit, double2* __restrict__ lam,
+              AdjPt* __restrict__ pts, int P) {
+  const int b = blockIdx.x;
+  if (b >= batch) return;  // block-uniform
+  const int32_t* mh = match_hit + (int64_t)b * obs.n_obs;
+  AdjPt* pp = pts + (int64_t)b * P;
+  double2* lb = lam + (int64_t)b * obs.n_obs;
+  for (int m = threadIdx.x; m < obs.n_obs; m += kAdjLamThreads) {
+    const int h = mh[m];
+    if (!adj_owner(mh, m, h)) {
+      for (int v = 0; v < 3; ++v) pp[3 * m + v] = AdjPt{0.0, 0.0, 0.0, 0.0};
+      lb[m] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const Hit H = hits[(int64_t)b * hit_cap + h];
+    // dchi^2/dx of this predicted image, over every observed image matched to it
+    double Gx = 0.0, Gy = 0.0;
+    for (int k = m; k < obs.n_obs; ++k) {
+      if (mh[k] != h) continue;
+      const double s2 = obs.sigma[k] * obs.sigma[k];
+      Gx += -2.0 * (obs.x[k] - H.x) / s2;
+      Gy += -2.0 * (obs.y[k] - H.y) / s2;
+    }
+    const double r = obs.dls_ds[obs.sys[m]];
+    double TX[3], TY[3], BX[3], BY[3];
+    for (int v = 0; v < 3; ++v) {
+      const AdjPt q = pp[3 * m + v];
+      TX[v] = q.x;
+      TY[v] = q.y;
+      BX[v] = TX[v] - r * q.cx;
+      BY[v] = TY[v] - r * q.cy;
+    }
+    const double M00 = BX[1] - BX[0], M01 = BX[2] - BX[0];
+    const double M10 = BY[1] - BY[0], M11 = BY[2] - BY[0];
+    const double det = M00 * M11 - M01 * M10;
+    const double dB = Gx * (TX[1] - TX[0]) + Gy * (TY[1] - TY[0]);
+    const double dC = Gx * (TX[2] - TX[0]) + Gy * (TY[2] - TY[0]);
+    const double lx = (M11 * dB - M10 * dC) / det;
+    const double ly = (-M01 * dB + M00 * dC) / det;
+    lb[m] = make_double2(lx, ly);
+    for (int v = 0; v < 3; ++v)
+      pp[3 * m + v] = AdjPt{TX[v], TY[v], r * H.w[v] * lx, r * H.w[v] * ly};
   }
-  const double fct = -obs.dls_ds[i] / n;
-  pts[(int64_t)b * P + 3 * obs.n_obs + m] = AdjPt{obs.x[m], obs.y[m], fct * Lx, fct * Ly};
+  __syncthreads();  // every lambda of the sample is written
+  for (int m = threadIdx.x; m < obs.n_obs; m += kAdjLamThreads) {
+    const int i = obs.sys[m];
+    double Lx = 0.0, Ly = 0.0;
+    int n = 0;
+    for (int k = 0; k < obs.n_obs; ++k) {
+      if (obs.sys[k] != i) continue;
+      ++n;
+      Lx += lb[k].x;
+      Ly += lb[k].y;
+    }
+    const double fct = -obs.dls_ds[i] / n;
+    pp[3 * obs.n_obs + m] = AdjPt{obs.x[m], obs.y[m], fct * Lx, fct * Ly};
+  }
 }
 
 // --------------------------------------------------------------- Jacobians
@@ -260,17 +293,23 @@ __device__ __forceinline__ void contract(const Pot64& P, float x, float y, float
 // One warp per (sample, potential): lane l takes adjoint points l, l + 32, ...;
 // each round of 32 points is reduced across the warp in FP32 (a fixed
 // butterfly, so the result is deterministic) and accumulated in FP64.
+// One block per (sample, potential): warp w takes the point chunks
+// 32 w, 32 w + kAdjThreads, ...; each chunk's FP32 warp sum is accumulated
+// in FP64 per warp, and the warps' sums are added in warp order (a fixed
+// order: the gradient is deterministic).
 __global__ void __launch_bounds__(kAdjThreads)
     k_adj_grad(const Pot64* __restrict__ pot64, int n_pot, int batch,
                const AdjPt* __restrict__ pts, int P, double* __restrict__ grad) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = ((int64_t)blockIdx.x * kAdjThreads + threadIdx.x) >> 5;
-  if (wid >= (int64_t)batch * n_pot) return;  // warp-uniform
-  const int b = (int)(wid / n_pot);
-  const Pot64 p = pot64[wid];
+  constexpr int NW = kAdjThreads / 32;
+  __shared__ double part[NW][6];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t pid = blockIdx.x;  // sample * n_pot + potential
+  if (pid >= (int64_t)batch * n_pot) return;  // block-uniform
+  const int b = (int)(pid / n_pot);
+  const Pot64 p = pot64[pid];
   const AdjPt* pb = pts + (int64_t)b * P;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int c0 = 0; c0 < P; c0 += 32) {
+  for (int c0 = 32 * w; c0 < P; c0 += kAdjThreads) {
     float o[6] = {0, 0, 0, 0, 0, 0};
     const int v = c0 + lane;
     if (v < P) {
@@ -286,7 +325,13 @@ __global__ void __launch_bounds__(kAdjThreads)
     }
   }
   if (lane == 0)
-    for (int m = 0; m < 6; ++m) grad[wid * 6 + m] = acc[m];
+    for (int m = 0; m < 6; ++m) part[w][m] = acc[m];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int k = 0; k < NW; ++k) s += part[k][threadIdx.x];
+    grad[pid * 6 + threadIdx.x] = s;
+  }
 }
 
 cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const SampleGrid* grids,
@@ -295,17 +340,17 @@ cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const Sampl
                            int sm_count, cudaStream_t st) {
   const int P = 4 * obs.n_obs;
   const int64_t warps = (int64_t)batch * obs.n_obs;
-  int64_t blocks = warps;
-  if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
-  k_adj_hits<<<(unsigned)blocks, kAdjHitThreads, 0, st>>>(pot64, n_pot, batch, grids, hits,
-                                                          hit_cap, obs, match_hit, lam, pts, P);
+  int64_t vblocks = warps * 3;
+  if (vblocks > (int64_t)sm_count * 16) vblocks = (int64_t)sm_count * 16;
+  k_adj_vtx<<<(unsigned)vblocks, kAdjVtxThreads, 0, st>>>(pot64, n_pot, batch, grids, hits,
+                                                          hit_cap, obs, match_hit, pts, P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_adj_bary<<<(unsigned)((warps + 127) / 128), 128, 0, st>>>(batch, obs, lam, pts, P);
+  k_adj_lam<<<(unsigned)batch, kAdjLamThreads, 0, st>>>(batch, hits, hit_cap, obs, match_hit,
+                                                        lam, pts, P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t gwarps = (int64_t)batch * n_pot;
-  const int64_t gblocks = (gwarps * 32 + kAdjThreads - 1) / kAdjThreads;
+  const int64_t gblocks = (int64_t)batch * n_pot;
   k_adj_grad<<<(unsigned)gblocks, kAdjThreads, 0, st>>>(pot64, n_pot, batch, pts, P, grad);
   return cudaGetLastError();
 }
