@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
   __shared__ float4 sp[kChunk32 * 5];
   __shared__ long long s_item;
   grid_dependency_wait();
+  int staged = -1;  // sample whose records sp holds (block-uniform)
   for (;;) {
     // dynamic distribution of the equal-size work items: blocks that start
     // late (another kernel still resident on their SM) simply take fewer
@@ -53,7 +54,8 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
 #pragma unroll
     for (int m = 0; m < NPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
     deflect32_nodes<NT, NPT, TIGHT>(pot32 + (int64_t)b * n_pot, n_pot, sg, g.theta_max, X, Y,
-                                    sp, AX, AY, ER);
+                                    sp, AX, AY, ER, staged != b);
+    staged = b;
     const float qs = TIGHT ? sg.q_tot : sg.c_tot;
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {

@@ -461,11 +461,15 @@ __device__ __forceinline__ void flush_lanes(NodeLanes<NPT>& AX, NodeLanes<NPT>& 
 // every operation of a node depends only on the potentials, not on NT, NPT or
 // the pairing of the thread's nodes.
 // sp: shared memory of kChunk32 * 5 float4; called by all NT threads.
+//
+// restage: false when sp already holds this sample's records (the block's
+// previous item was of the same sample and all its potentials fit one
+// chunk); the caller decides block-uniformly.
 template <int NT, int NPT, bool TIGHT>
 __device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, int n_pot,
                                                 const Seg32& sg, float theta1, float X,
                                                 const float* Y, float4* sp, float* AX,
-                                                float* AY, float* ER) {
+                                                float* AY, float* ER, bool restage = true) {
   typedef NodeLanes<NPT> NL;
   NL y, ax, ay, px, py, er;
 #pragma unroll
@@ -479,9 +483,11 @@ __device__ __forceinline__ void deflect32_nodes(const Pot32* __restrict__ pb, in
   }
   for (int c0 = 0; c0 < n_pot; c0 += kChunk32) {
     const int cn = min(kChunk32, n_pot - c0);
-    __syncthreads();  // the previous chunk's (or item's) readers of sp are done
-    stage_chunk32<NT>(sp, pb, c0, cn, sg, theta1);
-    __syncthreads();
+    if (restage || n_pot > kChunk32) {
+      __syncthreads();  // the previous chunk's (or item's) readers of sp are done
+      stage_chunk32<NT>(sp, pb, c0, cn, sg, theta1);
+      __syncthreads();
+    }
     const int e_sis = min(max(sg.n_sis - c0, 0), cn);
     const int e_pie = min(max(sg.n_sis + sg.n_piemd - c0, 0), cn);
     for (int k0 = 0; k0 < e_sis; k0 += kSumGroup) {

@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(kNT, kMinBlocks)
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
     // the batched kernel's body: the same operations in the same order
-    deflect32_nodes<kNT, kNPT, true>(pot32, n_pot, sg, theta1, X, Y, sp, AX, AY, ER);
+    deflect32_nodes<kNT, kNPT, true>(pot32, n_pot, sg, theta1, X, Y, sp, AX, AY, ER,
+                                     item == blockIdx.x);
 #pragma unroll
     for (int m = 0; m < kNPT; ++m) {
       if (live && j0 + m < g.ny) {
