@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
   __shared__ long long s_item;
   grid_dependency_wait();
   int staged = -1;  // sample whose records sp holds (block-uniform)
+  int b = 0;        // sample of the previous item: items arrive in increasing order
   for (;;) {
     // dynamic distribution of the equal-size work items: blocks that start
     // late (another kernel still resident on their SM) simply take fewer
@@ -36,7 +37,8 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
     __syncthreads();
     const int64_t item = s_item;
     if (item >= n_items) break;
-    int b = find_sample(item_off, n_samples, item);
+    if (item >= item_off[b + 1])  // a later sample: search from the previous one on
+      b += find_sample(item_off + b, n_samples - b, item);
     const SampleGrid g = grids[b];
     const Seg32 sg = seg[b];
     // this thread's column i and rows j0 .. j0 + NPT - 1 (see defl32_items)
