@@ -194,13 +194,16 @@ __device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, 
 // ------------------------------------------------- FP64 point deflections
 // Deflection at up to 3 points by a whole block of NT threads.  The threads
 // form one group of NT/npts per point; in each chunk of NT/npts potentials,
-// thread k of group q evaluates (point q, potential c0 + k), and then thread
-// q sums its point's chunk in potential index order, so the result is the
-// oracle's left-to-right sum exactly.  GB300's FP64 unit issues a warp
-// instruction only every few dozen cycles per SM sub-partition, so giving each
-// thread a single evaluation (NT >= npts * n_pot) keeps the serial FP64 depth
-// of a block at one potential.  Must be called by every thread of the block;
-// results in ax[q], ay[q] (shared); buf holds NT double2.
+// thread k of group q evaluates (point q, potential c0 + k), and then lanes
+// 2q and 2q + 1 of the first warp sum point q's x and y components over the
+// chunk in potential index order, so each result is the oracle's
+// left-to-right sum exactly.  GB300's FP64 unit issues a warp instruction
+// only every few dozen cycles per SM sub-partition, so giving each thread a
+// single evaluation (NT >= npts * n_pot) keeps the serial FP64 depth of a
+// block at one potential, and summing every component in one chain of warp
+// instructions keeps the sum's depth at one add per potential.  Must be
+// called by every thread of the block; results in ax[q], ay[q] (shared); buf
+// holds NT double2.
 template <int NT>
 __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, int npts,
                                      const double* px, const double* py, double* ax, double* ay,
@@ -208,7 +211,7 @@ __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, in
   const int t = threadIdx.x;
   const int G = NT / npts;
   const int q = t / G, k = t - q * G;
-  double sx = 0.0, sy = 0.0;
+  double sum = 0.0;  // summing lanes: component t & 1 of point t >> 1
   for (int c0 = 0; c0 < n_pot; c0 += G) {
     if (q < npts && c0 + k < n_pot) {
       const Pot64 p = pb[c0 + k];
@@ -217,20 +220,14 @@ __device__ inline void block_alpha64(const Pot64* __restrict__ pb, int n_pot, in
       buf[q * G + k] = make_double2(kx, ky);
     }
     __syncthreads();
-    if (t < npts) {
+    if (t < 2 * npts) {
       const int cn = min(G, n_pot - c0);
-      for (int m = 0; m < cn; ++m) {
-        const double2 v = buf[t * G + m];
-        sx = sx + v.x;
-        sy = sy + v.y;
-      }
+      const double* col = reinterpret_cast<const double*>(buf + (t >> 1) * G) + (t & 1);
+      for (int m = 0; m < cn; ++m) sum = sum + col[2 * m];
     }
     __syncthreads();
   }
-  if (t < npts) {
-    ax[t] = sx;
-    ay[t] = sy;
-  }
+  if (t < 2 * npts) (t & 1 ? ay : ax)[t >> 1] = sum;
   __syncthreads();
 }
 
