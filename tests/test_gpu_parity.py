@@ -76,6 +76,33 @@ def test_deflect_fp64_matches_oracle(oracle, seed):
     assert np.all(err <= 1e-12 * (asum + 1.0)), err.max()
 
 
+def test_deflect_fp64_bit_exact_correctly_rounded(oracle):
+    """SIS and axis-aligned SIE (phi = 0: cos and sin exactly 1 and 0) use only
+    correctly rounded FP64 operations (+, -, *, /, sqrt) in the oracle's order,
+    so the FP64 grid, superposed in potential index order (Sect. 2.2.2),
+    equals the oracle bit for bit.  300 potentials span several staged chunks;
+    some centres fall exactly on nodes (the zero-distance branch)."""
+    rng = np.random.default_rng(23)
+    n = 300
+    p = np.zeros((W.N_ROWS, n))
+    p[0] = rng.choice([W.SIS, W.SIE], n)
+    p[1] = rng.uniform(-40.0, 40.0, n)
+    p[2] = rng.uniform(-40.0, 40.0, n)
+    p[1, :20] = rng.integers(-80, 81, 20) * 0.5  # on nodes of the grid below
+    p[2, :20] = rng.integers(-80, 81, 20) * 0.5
+    p[3] = np.where(p[0] == W.SIE, rng.uniform(0.0, 0.6, n), 0.0)
+    p[7] = rng.uniform(50.0, 400.0, n)
+    p[7, :2] = [900.0, 700.0]
+    grid = (-40.0, -40.0, 0.5, 0.5, 161, 161)
+    m = lt.Model(n, 1)
+    m.set_params(p[None])
+    a = m.deflect_grid(grid, precision=lt.FP64).cpu().numpy()
+    assert m.sync()[0] == lt.LT_OK
+    m.close()
+    ref, _ = oracle.deflect_grid(p, grid, n_threads=4)
+    np.testing.assert_array_equal(a, ref)
+
+
 @pytest.mark.parametrize("seed", [3, 4, 5])
 def test_deflect_mixed_within_running_bound(oracle, seed):
     p = mixed_cluster(seed, n_pot=40)
