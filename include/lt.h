@@ -50,7 +50,7 @@ typedef enum {
   LT_ERR_NOMEM = 3,       /* device allocation failed */
   LT_ERR_OVERFLOW = 4,    /* more hits / FP64 work items than capacity */
   LT_ERR_TIMEOUT = 5,     /* reserved: no kernel of this library spin-waits */
-  LT_ERR_NONFINITE = 6    /* non-finite or out-of-domain lens parameter */
+  LT_ERR_NONFINITE = 6    /* non-finite or out-of-domain lens parameter or source */
 } lt_status;
 
 typedef enum { LT_SIS = 0, LT_PIEMD = 1, LT_SIE = 2 } lt_kind;
@@ -187,7 +187,10 @@ lt_status lt_deflect_grid(lt_model* model, int32_t sample, const lt_grid* grid,
  * [batch][n_src]; out: device [batch][capacity] lt_image records, each
  * sample's images sorted by (src, tri); n_out: device [batch] int64, the
  * number of images of each sample (may exceed capacity: then only capacity
- * records are written and LT_ERR_OVERFLOW is latched).
+ * records are written and LT_ERR_OVERFLOW is latched).  A source needs a
+ * finite position and a ratio 0 <= D_ls/D_s < 1e30 (0: a source in the lens
+ * plane, whose image is the source position itself); any other source has
+ * no images and LT_ERR_NONFINITE is latched.
  * Errors: LT_ERR_INVALID_ARG. */
 lt_status lt_find_images(lt_model* model, const lt_grid* grids, int32_t n_src,
                          const double* src_xy, const double* dls_ds, lt_precision precision,
@@ -198,7 +201,9 @@ lt_status lt_find_images(lt_model* model, const lt_grid* grids, int32_t n_src,
  * barycentric image positions, and for each observed image the nearest
  * predicted image of its system (ties to the lower triangle id); a system
  * with no predicted image contributes (L_diag/sigma)^2 per observed image,
- * L_diag the diagonal of its sample's grid.
+ * L_diag the diagonal of its sample's grid.  A system whose barycentre is not
+ * finite or whose D_ls/D_s lies outside [0, 1e30) has no predicted images
+ * (LT_ERR_NONFINITE latched), as in lt_find_images.
  * grids: host [batch]; obs: host struct of device pointers; chi2_out: device
  * [batch] double.  Errors: LT_ERR_INVALID_ARG; overflow latched. */
 lt_status lt_chi2(lt_model* model, const lt_grid* grids, const lt_obs* obs,

@@ -510,6 +510,12 @@ __global__ void __launch_bounds__(kSearch64Threads)
     const double* sr = src.r + (int64_t)sample * src.n_src * (src.stride_r ? 1 : 0);
     for (int k = 0; k < src.n_src; ++k) {
       const double Px = sxy[2 * k], Py = sxy[2 * k + 1], r = sr[k];
+      // the mixed path's input domain: a finite position and 0 <= r < 1e30;
+      // anything else is latched and the source has no images
+      if (!(isfinite(Px) && isfinite(Py) && r >= 0.0 && r < 1e30)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+        continue;
+      }
       // mapped vertices beta = theta - r alpha (Eq. 13)
       const double b00x = X0 - r * a00.x, b00y = Y0 - r * a00.y;
       const double b10x = X1 - r * a10.x, b10y = Y0 - r * a10.y;

@@ -304,8 +304,14 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
       if (!whole || staged != sample) {
         __syncwarp();  // earlier readers of ss are done
         for (int v = lane; v < sn; v += kSearchThreads) {
-          const float px = (float)sxy[2 * (s0 + v)], py = (float)sxy[2 * (s0 + v) + 1];
-          ss[v] = SrcSmem{px, py, (float)sr[s0 + v],
+          const double pxd = sxy[2 * (s0 + v)], pyd = sxy[2 * (s0 + v) + 1], rd = sr[s0 + v];
+          // searched only with a finite position and a ratio 0 <= r < 1e30
+          // (Eq. 13); otherwise latched, and the NaN ratio fails every
+          // comparison of the cull, so the source has no images
+          const bool ok = isfinite(pxd) && isfinite(pyd) && rd >= 0.0 && rd < 1e30;
+          if (!ok) atomicOr(status, ST_NONFINITE);
+          const float px = (float)pxd, py = (float)pyd;
+          ss[v] = SrcSmem{px, py, ok ? (float)rd : __int_as_float(0x7fffffff),
                           __fmul_ru(u, __fmaf_ru(4.0f, g.theta_max,
                                                  __fadd_ru(fabsf(px), fabsf(py))))};
         }

@@ -299,6 +299,100 @@ def test_find_images_sis(oracle, prec, tol):
     check_images(oracle, w.params[0], g, src, [0.7] * len(src), prec, tol, exact_ties=True)
 
 
+def degenerate_lens():
+    """The c1 SIS with zero-mass SIS, SIE (phi = 0) and PIEMD potentials and a
+    light SIS centred exactly on grid nodes next to the images of the source
+    (2, 1.5) at r = 0.7 (near (-6.0, -4.5) and (10.0, 7.5)).  Every operation
+    of this lens is correctly rounded (a zero-mass PIEMD adds exactly zero)."""
+    w = W.c1()
+    g = w.grids[0].as_tuple()
+    x0, y0, dx, dy = g[:4]
+    node = lambda i, j: (x0 + i * dx, y0 + j * dy)  # the grid's own node formula
+    i1, j1 = round((-6.0 - x0) / dx), round((-4.5 - y0) / dy)
+    i2, j2 = round((10.0 - x0) / dx), round((7.5 - y0) / dy)
+    spots = [(W.SIS, node(i1, j1), 0.0), (W.PIEMD, node(i1 + 1, j1), 0.0),
+             (W.SIE, node(i2, j2), 0.0), (W.SIS, node(i2 + 2, j2 - 1), 40.0)]
+    p = np.zeros((W.N_ROWS, 1 + len(spots)))
+    p[:, 0] = w.params[0, :, 0]
+    for k, (kind, (x, y), sv) in enumerate(spots, start=1):
+        p[0, k], p[1, k], p[2, k], p[7, k] = kind, x, y, sv
+        if kind != W.SIS:
+            p[3, k] = 0.3
+        if kind == W.PIEMD:
+            p[5, k], p[6, k] = 0.5, 20.0
+    centres = [(i1, j1), (i2, j2), (i2 + 2, j2 - 1)]  # SIS / SIE centres on nodes
+    return p, g, centres
+
+
+def test_deflect_degenerate_potentials(oracle):
+    """Nodes on SIS / SIE centres (zero-mass ones included): the FP32
+    deflection is finite there and equals the oracle's limit value, and the
+    node's running bound is the 1e30 that marks no bound (never NaN), so no
+    test is certified with it; every other node stays within its own bound."""
+    p, g, centres = degenerate_lens()
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    a, e = m.deflect_grid(g, precision=lt.MIXED, with_error=True)
+    assert m.sync()[0] == lt.LT_OK
+    a, e = a.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a)) and not np.any(np.isnan(e))
+    on = np.zeros(e.shape, bool)
+    for i, j in centres:
+        on[j, i] = True
+    assert np.all(e[on] == float(np.float32(1e30))) and np.all(e[~on] < 1.0)
+    ref, _ = oracle.deflect_grid(p, g, n_threads=4)
+    d = np.abs(a - ref).max(axis=-1)
+    assert np.all(d[~on] <= e[~on]), (d[~on] / e[~on]).max()
+    # on the centre nodes the massive SIS alone contributes (0 at its centre,
+    # exactly as the oracle); the difference is the FP32 rounding of the rest
+    assert np.all(d[on] <= 1e-4)
+
+
+@pytest.mark.parametrize("prec,tol", [(lt.FP64, 1e-9), (lt.MIXED, 1e-4)])
+def test_find_images_degenerate_potentials(oracle, prec, tol):
+    """Triangles with a vertex on a potential's centre (infinite FP32 bound)
+    go to the FP64 stage; the image set still equals the oracle's, ties
+    included (the lens's operations are all correctly rounded)."""
+    p, g, _ = degenerate_lens()
+    stats, _ = check_images(oracle, p, g, [(2.0, 1.5), (-1.0, 3.0)], [0.7, 0.7], prec, tol,
+                            exact_ties=True)
+    if prec == lt.MIXED:
+        assert stats["fp64_items"] > 0, stats
+
+
+@pytest.mark.parametrize("prec,tol", [(lt.FP64, 1e-9), (lt.MIXED, 1e-4)])
+def test_find_images_zero_ratio(oracle, prec, tol):
+    """D_ls/D_s = 0 (a source in the lens plane): beta = theta exactly, so the
+    image is the source position itself, decided by the tie rule where the
+    source sits on a node -- here nodes on SIS / SIE centres, whose infinite
+    FP32 bound (1e30) leaves the test to the FP64 stage."""
+    p, g, centres = degenerate_lens()
+    x0, y0, dx, dy = g[:4]
+    on = [(x0 + i * dx, y0 + j * dy) for i, j in centres]
+    src = [(2.0, 1.5), on[0], on[1], on[2], (3.3, -7.1), (2.0, 1.5)]
+    r = [0.0, 0.0, 0.0, 0.0, 0.0, 0.7]
+    check_images(oracle, p, g, src, r, prec, tol, exact_ties=True)
+
+
+@pytest.mark.parametrize("prec", [lt.FP64, lt.MIXED])
+def test_invalid_sources_are_latched(oracle, prec):
+    """A negative or NaN ratio, or a non-finite position, is outside the
+    input domain: LT_ERR_NONFINITE is latched and that source has no images,
+    while the valid sources' images equal the oracle's."""
+    p, g, _ = degenerate_lens()
+    src = [(2.0, 1.5), (2.0, 1.5), (-1.0, 3.0), (np.nan, 1.0), (-1.0, 3.0)]
+    r = [0.7, -0.5, np.nan, 0.7, 0.7]
+    valid = [0, 4]
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    st, stats, imgs, n = run_find(m, [g], np.asarray(src)[None], np.asarray(r)[None], prec)
+    assert st == lt.LT_ERR_NONFINITE
+    got = to_set(imgs[0])
+    assert {s_ for s_, _ in got} <= set(valid)
+    H, _ = oracle.find_images(p, g, [src[k] for k in valid], [r[k] for k in valid], n_threads=4)
+    assert got == {(valid[h["src"]], h["tri"]) for h in H}
+
+
 @pytest.mark.parametrize("seed", [11, 12])
 @pytest.mark.parametrize("prec,tol", [(lt.FP64, 1e-9), (lt.MIXED, 1e-4)])
 def test_find_images_cluster(oracle, seed, prec, tol):
