@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(kPrepThreads)
     p.sc = v[LT_ROW_RCUT];
     p.scale = kind == LT_PIEMD ? p.b0 * (p.sc / (p.sc - p.a)) : 0.0;
     p.sv = v[LT_ROW_SIGMA];
-    p.pad1 = p.pad2 = 0.0;
+    p.k = sqrt(p.k2);
+    p.ik = p.k > 0.0 ? 1.0 / p.k : 0.0;
     p64[k] = p;
     atomicAdd(&cnt[kind], 1);
   }

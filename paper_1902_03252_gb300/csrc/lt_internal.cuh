@@ -37,11 +37,13 @@ constexpr float kU32 = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
 
 // --------------------------------------------------------- prepared records
 // FP64 record of one potential, in parameter index order (16 doubles).  The
-// FP64 path sums potentials in index order with the formula order stated in
-// alpha64_one, so it reproduces an FP64 reference that follows the same
-// statement up to the ulps of the transcendental functions.
+// FP64 path sums potentials in index order with the formulas of alpha64_one:
+// the SIS and SIE as stated there (an FP64 reference that follows the same
+// statement is reproduced to the ulps of sin and cos), the PIEMD in the
+// difference form (a few ulps of the deflection).  k = sqrt(k2), ik = 1/k (0
+// for k = 0).
 struct Pot64 {
-  double kind, cx, cy, c, s, b0, e, q, k2, q2, a, sc, scale, sv, pad1, pad2;
+  double kind, cx, cy, c, s, b0, e, q, k2, q2, a, sc, scale, sv, k, ik;
 };
 static_assert(sizeof(Pot64) == 128, "Pot64 layout");
 
@@ -123,17 +125,18 @@ constexpr int kChunk32 = 256;
 constexpr int kSumGroup = 32;
 
 // ---------------------------------------------------- FP64 deflection (one)
-// atan(t)/t and atanh(t)/t as functions of t2 = t*t, with the short Taylor
-// branch for tiny arguments (keeps q -> 1 exact).
-__device__ __forceinline__ double atanc_sq64(double t2) {
-  if (t2 < 1e-6) return 1.0 - t2 * (1.0 / 3.0 - t2 * (1.0 / 5.0 - t2 * (1.0 / 7.0)));
-  double t = sqrt(t2);
-  return atan(t) / t;
+// atan(k T)/k and atanh(k T)/k of a record's k = sqrt(k2) and ik = 1/k: the
+// short Taylor series in u = k2 T^2 below 1e-6 (which also covers k = 0 and
+// keeps the q -> 1 limit exact), else the library function times 1/k.
+__device__ __forceinline__ double atan_k64(double T, double k, double ik, double k2) {
+  const double u = k2 * T * T;
+  if (u < 1e-6) return T * (1.0 - u * (1.0 / 3.0 - u * (1.0 / 5.0 - u * (1.0 / 7.0))));
+  return atan(k * T) * ik;
 }
-__device__ __forceinline__ double atanhc_sq64(double t2) {
-  if (t2 < 1e-6) return 1.0 + t2 * (1.0 / 3.0 + t2 * (1.0 / 5.0 + t2 * (1.0 / 7.0)));
-  double t = sqrt(t2);
-  return atanh(t) / t;
+__device__ __forceinline__ double atanh_k64(double T, double k, double ik, double k2) {
+  const double u = k2 * T * T;
+  if (u < 1e-6) return T * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
+  return atanh(k * T) * ik;
 }
 
 // Scaled deflection of one potential at (x, y) in FP64.  Must be compiled
@@ -142,10 +145,17 @@ __device__ __forceinline__ double atanhc_sq64(double t2) {
 //   SIS  (Sect. 2.1): b0 (theta - c)/|theta - c|, zero at the centre.
 //   SIE  (Algorithm 1): translate, rotate by phi, R = sqrt(x'^2 (1-eps) +
 //        y'^2 (1+eps)), ((1-eps) b0 x'/R, (1+eps) b0 y'/R), rotate by -phi.
-//   PIEMD (dPIE core a, cut s, q = 1 - e): per cored term w in (a, s)
-//        psi = sqrt(q^2 (w^2 + x'^2) + y'^2), zx = x'/(psi + w),
-//        zy = y'/(psi + q^2 w), F = (zx atanc(k^2 zx^2), zy atanhc(k^2 zy^2));
-//        alpha' = b0 s/(s-a) [F(a) - F(s)], rotated by -phi.
+//   PIEMD (dPIE core a, cut s, q = 1 - e): alpha' = b0 s/(s-a) [F(a) - F(s)]
+//        rotated by -phi, with per cored term w in (a, s) psi_w = sqrt(q^2
+//        (w^2 + x'^2) + y'^2) and F(w) = (atan(k x'/(psi_w + w)),
+//        atanh(k y'/(psi_w + q^2 w)))/k, evaluated in difference form: with
+//        atan u - atan v = atan((u - v)/(1 + uv)), the atanh analogue and
+//        psi_s - psi_a = q^2 (s^2 - a^2)/(psi_a + psi_s),
+//          F_x(a) - F_x(s) = atan(k Tx)/k, Tx = x' (s-a)(1 + q^2 (s+a)/(psi_a
+//            + psi_s)) / ((psi_a + a)(psi_s + s) + k^2 x'^2),
+//          F_y(a) - F_y(s) = atanh(k Ty)/k, Ty = y' q^2 (s-a)(1 + (s+a)/(psi_a
+//            + psi_s)) / ((psi_a + q^2 a)(psi_s + q^2 s) - k^2 y'^2),
+//        one atan and one atanh instead of two each (the FP32 path's form).
 __device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, double& ax,
                                             double& ay) {
   double dx = x - p.cx;
@@ -167,25 +177,18 @@ __device__ __forceinline__ void alpha64_one(const Pot64& p, double x, double y, 
     gx = (1.0 - p.e) * p.b0 * xp / R;
     gy = (1.0 + p.e) * p.b0 * yp / R;
   } else {
-    double fx0, fy0, fx1, fy1;
-    {
-      double w = p.a;
-      double psi = sqrt(p.q2 * (w * w + xp * xp) + yp * yp);
-      double zx = xp / (psi + w);
-      double zy = yp / (psi + p.q2 * w);
-      fx0 = zx * atanc_sq64(p.k2 * zx * zx);
-      fy0 = zy * atanhc_sq64(p.k2 * zy * zy);
-    }
-    {
-      double w = p.sc;
-      double psi = sqrt(p.q2 * (w * w + xp * xp) + yp * yp);
-      double zx = xp / (psi + w);
-      double zy = yp / (psi + p.q2 * w);
-      fx1 = zx * atanc_sq64(p.k2 * zx * zx);
-      fy1 = zy * atanhc_sq64(p.k2 * zy * zy);
-    }
-    gx = p.scale * (fx0 - fx1);
-    gy = p.scale * (fy0 - fy1);
+    const double x2 = xp * xp, y2 = yp * yp;
+    const double t = p.q2 * x2 + y2;
+    const double pa = sqrt(t + p.q2 * (p.a * p.a));
+    const double ps = sqrt(t + p.q2 * (p.sc * p.sc));
+    const double iD = 1.0 / (pa + ps);
+    const double sa = p.sc - p.a;
+    const double Tx = xp * (sa * (1.0 + p.q2 * (p.sc + p.a) * iD)) /
+                      ((pa + p.a) * (ps + p.sc) + p.k2 * x2);
+    const double Ty = yp * (p.q2 * sa * (1.0 + (p.sc + p.a) * iD)) /
+                      ((pa + p.q2 * p.a) * (ps + p.q2 * p.sc) - p.k2 * y2);
+    gx = p.scale * atan_k64(Tx, p.k, p.ik, p.k2);
+    gy = p.scale * atanh_k64(Ty, p.k, p.ik, p.k2);
   }
   ax = gx * p.c - gy * p.s;
   ay = gy * p.c + gx * p.s;
