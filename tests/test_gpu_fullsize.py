@@ -241,3 +241,68 @@ def test_c5_work_overflow_is_reported():
     assert st == lt.LT_ERR_OVERFLOW
     assert stats["work_overflow"] > 0
     m.close()
+
+
+def test_find_images_beyond_int32_nodes(oracle):
+    """The largest case: a 46400^2 grid, 2.15e9 nodes (more than 2^31, a 34 GB
+    node workspace), one SIS (c1), four sources in mixed precision -- the
+    64-bit index paths of the deflection, the search and the image records.
+    The grid's top rows hold cells beyond 2^31 and triangle ids beyond 2^32,
+    where the outer image of the source (0, 1.9) falls.  The grid is dyadic
+    (dx = 2^-9), so a patch of it starting at node (i0, j0) has bit-identical
+    node coordinates: the oracle searches patches around the closed-form SIS
+    image positions and the lens centre (a node, where the FP32 bound is
+    1e30), and the union of its images, with ids mapped to the full grid,
+    must equal the GPU's image set (exact ties included: the source (2, 1.5)
+    has its images on nodes, and every operation of the lens is correctly
+    rounded), with the positions."""
+    w = W.c1()
+    p = w.params[0]
+    n = 46400
+    dx = 2.0 ** -9
+    x0 = -(n // 2) * dx
+    y0 = 12.0 - (n - 1) * dx
+    grid = (x0, y0, dx, dx, n, n)
+    src = np.array([(0.0, 1.9), (2.0, 1.5), (-4.0, 6.0), (0.3, -0.2)])
+    r = np.full(len(src), 0.7)
+    m = lt.Model(1, 1, hit_capacity=4096)
+    m.set_params(p[None])
+    sx = torch.as_tensor(src[None], device="cuda")
+    rr = torch.as_tensor(r[None], device="cuda")
+    out, cnt = m.find_images([grid], sx, rr, precision=lt.MIXED, capacity=4096)
+    st, stats = m.sync()
+    assert st == lt.LT_OK, (st, stats)
+    imgs = lt.images_to_numpy(out, cnt)[0]
+    m.close()
+    del out
+    torch.cuda.empty_cache()
+    got = {(int(h["src"]), int(h["tri"])): h for h in imgs}
+    # closed form: the SIS maps theta to beta = theta - r b0 theta/|theta|, so
+    # the images lie on the source's direction at |beta| + r b0 and r b0 - |beta|
+    thE = 0.7 * (4.0 * math.pi * (p[7, 0] / 299792.458) ** 2 * 206264.80625)
+    half = 16
+    exp = {}
+    for k, (bx, by) in enumerate(src):
+        b = math.hypot(bx, by)
+        spots = [(bx / b * (b + thE), by / b * (b + thE)),
+                 (-bx / b * (thE - b), -by / b * (thE - b)), (0.0, 0.0)]
+        for (tx, ty) in spots:
+            i0 = max(0, int(round((tx - x0) / dx)) - half)
+            j0 = max(0, int(round((ty - y0) / dx)) - half)
+            i1 = min(n - 1, i0 + 2 * half)
+            j1 = min(n - 1, j0 + 2 * half)
+            if i1 - i0 < 2 or j1 - j0 < 2:  # the image is off the grid
+                continue
+            pw = i1 - i0 + 1
+            patch = (x0 + i0 * dx, y0 + j0 * dx, dx, dx, pw, j1 - j0 + 1)
+            H, _ = oracle.find_images(p, patch, [(bx, by)], [0.7], n_threads=4)
+            for h in H:
+                cell = h["tri"] // 2
+                ci, cj = cell % (pw - 1), cell // (pw - 1)
+                tri = 2 * ((j0 + cj) * (n - 1) + (i0 + ci)) + h["tri"] % 2
+                exp[(k, tri)] = h
+    assert max(t for _, t in exp) > 2 ** 32  # ids beyond 32 bits are exercised
+    assert set(got) == set(exp), (sorted(set(got) ^ set(exp))[:10], len(got), len(exp))
+    worst = max(max(abs(got[key]["x"] - h["x"]), abs(got[key]["y"] - h["y"]))
+                for key, h in exp.items())
+    assert worst <= 1e-4, worst
