@@ -32,6 +32,46 @@ __device__ __forceinline__ int find_sample64(const int64_t* off, int n, int64_t 
 // ------------------------------------------------------------- preparation
 constexpr int kPrepThreads = 256;
 
+// The error-bound coefficients are formed in FP32 with directed rounding
+// (GB300 issues an FP64 warp instruction only every ~80 cycles per SM
+// sub-partition, and this kernel is one chain of them per potential): every
+// quantity that enlarges a bound is rounded up, every divisor down, so each
+// result is an upper bound of its formula's exact value.  Constants are
+// evaluated in FP64 at compile time and rounded up to float (cup: a relative
+// 2^-22 above the value, more than the 2^-24 of the rounding to float).
+constexpr double cU = kU32d;
+constexpr float cup(double x) { return (float)(x * (1.0 + 0x1p-22)); }
+constexpr double gamc(double n) { return n / (1.0 - n * cU); }  // gamma(n) for n u << 1
+// gamma(n) = n / (1 - n u) of a runtime n >= 0, rounded up; 1e30 once n u >= 1/4
+__device__ __forceinline__ float gam_up(float n) {
+  const float nu = __fmul_ru(n, kU32);
+  return nu >= 0.25f ? 1e30f : __fdiv_ru(n, __fsub_rd(1.0f, nu));
+}
+constexpr double cM7 = 4.0 + (kEpsRsqrt > kEpsSqrt - 1.0 ? kEpsRsqrt : kEpsSqrt - 1.0) + kEpsRcp;
+constexpr double cNtx = cM7 + 13.0 + kEpsRsqrt + kEpsSqrt + kEpsRcp;
+// SIS: P, Q, Q2 and T per unit b0
+constexpr float kP0Sis = cup(8.0 * (1.0 + cU) / ((1.0 - 3.1 * cU) * (1.0 - (1.01 + kEpsRsqrt) * cU)));
+constexpr float kQSis = cup(gamc(3.0 + kEpsRsqrt) + 3.0 * (1.0 + 3.0 * cU));
+constexpr float kQ2Sis = cup(gamc(3.0 + kEpsRsqrt) + 1.01);
+constexpr float kTSis = cup(1.41421357 * (1.0 + gamc(5.0 + kEpsRsqrt) * cU));
+// SIE: per unit b0 r2 (and 1/r1 terms)
+constexpr float kP0Sie = cup(11.32 * (1.0 + 3.0 * cU) / (1.0 - (1.01 + kEpsRsqrt) * cU));
+constexpr float kP0SieR1 = cup(16.1 * cU);
+constexpr float kGSie = cup(gamc(5.25 + kEpsRsqrt));
+constexpr float kQSieR1 = cup(16.04 * (1.0 + 3.0 * cU));
+constexpr float kQ2SieR1 = cup(10.1 * (1.0 + 3.0 * cU));
+constexpr float kTSie = cup(1.41421357 * (1.0 + gamc(6.25 + kEpsRsqrt) * cU));
+// PIEMD
+constexpr float kC8 = cup(8.0 + kEpsRsqrt + kEpsSqrt);
+constexpr float kNty0 = cup(cM7 + 4.0 + kEpsRcp);
+constexpr float kGx = cup(gamc(cNtx + kEpsAtanc + 3.5));
+constexpr float kEpsAtanhcF = cup(kEpsAtanhc), kEpsAtanhcLogF = cup(kEpsAtanhcLog);
+constexpr float kP0Piemd = cup(2.8285 * (1.0 + 3.0 * cU) / (1.0 - (2.0 + kEpsRsqrt) * cU));
+constexpr float kQPiemd = cup(16.04 * (1.0 + 3.0 * cU));
+constexpr float kQ2Piemd = cup(10.1 * (1.0 + 3.0 * cU));
+constexpr float kAtanF = cup(1.0 + (kEpsAtanc + 0.1) * cU);
+constexpr float kT2u = cup(1.0 + 2.0 * cU);
+
 __device__ __forceinline__ bool valid_params(const double* v, int* kind_out) {
   bool ok = true;
   for (int r = 0; r < LT_N_ROWS; ++r) ok = ok && isfinite(v[r]);
@@ -173,9 +213,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     //    the kernel;
     //  * second order: counted units n enter as gamma(n) = n / (1 - n u)
     //    (Higham, Accuracy and Stability of Numerical Algorithms, Lemma 3.1).
-    const double U = kU32d;
-    auto gam = [U](double n) { return n * U >= 0.25 ? 1e30 : n / (1.0 - n * U); };
-    double Q, T, Q2, Gmax = 0.0;
+    float Q, T, Q2, Gmax = 0.0f;
     if (kind == LT_SIS) {
       // Jacobian of b0 n(Delta): b0/|Delta| (2-norm).  Where |D| >= 2|e|:
       // error <= 2 b0 |e| / |D| with |e| <= u(1+u)(W2 + |Delta|), W2 =
@@ -185,16 +223,16 @@ __global__ void __launch_bounds__(kPrepThreads)
       // P >= 4 b0 |e| / u: P = 8 b0 W.  rr = rsqrt(R2) errs by (1.01 + eps_r) u.
       // Evaluation: b0 (1 u), R2 (2 u, halved by the root), rsqrt, b0 * rr
       // (1 u): 3 + eps_r relative, |alpha_k| <= b0, into Q.
-      const double p0 = 8.0 * p.b0 * (1.0 + U) / ((1.0 - 3.1 * U) * (1.0 - (1.01 + kEpsRsqrt) * U));
+      const float b0u = __double2float_ru(p.b0);
       f.f[0] = make_float4(cx, cy, (float)p.b0, 0.f);
-      f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
-      Q = p.b0 * (gam(3.0 + kEpsRsqrt) + 3.0 * (1.0 + 3.0 * U));
+      f.f[4] = make_float4(__fmul_ru(kP0Sis, b0u), 0.f, 0.f, 0.f);
+      Q = __fmul_ru(kQSis, b0u);
       // tight re-evaluation (node translated in FP64, rounded once: error
       // u (1 + 2^-28) |Delta| per coordinate, so |e| <= 1.0001 u |Delta|):
       // the Jacobian b0/|Delta| gives 1.01 u b0, with the evaluation terms
-      Q2 = p.b0 * (gam(3.0 + kEpsRsqrt) + 1.01);
+      Q2 = __fmul_ru(kQ2Sis, b0u);
       // |t_x| + |t_y| = g (|dx| + |dy|) <= sqrt(2) b0 (1 + (3 + eps_r) u)
-      T = 1.41421357 * p.b0 * (1.0 + gam(5.0 + kEpsRsqrt) * U);
+      T = __fmul_ru(kTSis, b0u);
     } else if (kind == LT_SIE) {
       const double r1 = sqrt(1.0 - p.e), r2 = sqrt(1.0 + p.e);
       // z = (r1 x', r2 y'), g = b0 diag(r1, r2) z / |z|: Jacobian in z at most
@@ -208,21 +246,23 @@ __global__ void __launch_bounds__(kPrepThreads)
       // three roundings on each product term, |t| <= b0 r2 R, so
       // |t_FP32 - t| <= 3 sqrt(2) u b0 r2 R; times rr ((1.01 + eps_r) u):
       // (5.25 + eps_r) b0 r2 into Q.
-      const double p0 = 11.32 * p.b0 * r2 * (1.0 + 3.0 * U) /
-                        ((1.0 - 16.1 * U / r1) * (1.0 - (1.01 + kEpsRsqrt) * U));
+      const float r1d = __double2float_rd(r1);
+      const float b0r2 = __fmul_ru(__double2float_ru(p.b0), __double2float_ru(r2));
+      const float den1 = __fsub_rd(1.0f, __fdiv_ru(kP0SieR1, r1d));
+      const float p0 = den1 > 0.0f ? __fdiv_ru(__fmul_ru(kP0Sie, b0r2), den1) : 1e30f;
       f.f[0] = make_float4(cx, cy, (float)(r1 * p.c), (float)(r1 * p.s));
       f.f[1] = make_float4((float)(r2 * p.c), (float)(r2 * p.s), (float)(p.b0 * r1 * p.c),
                            (float)(p.b0 * r2 * p.s));
       f.f[2] = make_float4((float)(p.b0 * r2 * p.c), (float)(p.b0 * r1 * p.s), 0.f, 0.f);
-      f.f[4] = make_float4(__double2float_ru(p0), 0.f, 0.f, 0.f);
-      Q = p.b0 * r2 * (gam(5.25 + kEpsRsqrt) + 16.04 * (1.0 + 3.0 * U) / r1);
+      f.f[4] = make_float4(p0, 0.f, 0.f, 0.f);
+      Q = __fmul_ru(b0r2, __fadd_ru(kGSie, __fdiv_ru(kQSieR1, r1d)));
       // tight re-evaluation: translation error 1.0001 u |Delta|_1 and the
       // rotation's 4.01 u |Delta|_1, so |e_z| <= sqrt(2) 5.02 u (1+3u) |Delta|_1
       // <= 10.04 u (1+3u) |z| / r1, far below |z| / 2: 10.1 b0 r2 / r1 with
       // the evaluation terms (r1 < 1e-3 is not bounded)
-      Q2 = r1 < 1e-3 ? 1e30 : p.b0 * r2 * (gam(5.25 + kEpsRsqrt) + 10.1 * (1.0 + 3.0 * U) / r1);
+      Q2 = r1 < 1e-3 ? 1e30f : __fmul_ru(b0r2, __fadd_ru(kGSie, __fdiv_ru(kQ2SieR1, r1d)));
       // |t_x| + |t_y| <= sqrt(2) |rr (t1, t2)| <= sqrt(2) b0 r2 (1 + (6.25 + eps_r) u)
-      T = 1.41421357 * p.b0 * r2 * (1.0 + gam(6.25 + kEpsRsqrt) * U);
+      T = __fmul_ru(kTSie, b0r2);
     } else {
       const double a = p.a, sc = p.sc, q2 = p.q2, q = p.q;
       const double B = p.scale;
@@ -253,20 +293,28 @@ __global__ void __launch_bounds__(kPrepThreads)
       //   g_y = atanh(t_y): elasticity <= 1/(1 - t_y^2) <= 1/q^2 (|t_y| < k),
       //   the square at k2/(2 q^2), eps_atanhc, 1 u.  Two more units for the
       //   rounded (Bc, Bs) and the inner FMA of the accumulation.
-      const double m7 = 4.0 + fmax(kEpsRsqrt, kEpsSqrt - 1.0) + kEpsRcp;
-      const double n_tx = m7 + 13.0 + kEpsRsqrt + kEpsSqrt + kEpsRcp;
-      const double iq2 = 1.0 / q2;
-      const double c_dy = (8.0 + kEpsRsqrt + kEpsSqrt + 2.0 * p.k2) * iq2 + 1.0;
-      const double n_ty = m7 + 4.0 + kEpsRcp + c_dy;
+      // (m7 = 4 + max(eps_r, eps_s - 1) + eps_rcp, n_tx = m7 + 13 + eps_r +
+      // eps_s + eps_rcp: constants, folded into kNty0 and kGx.)
+      const float qd = __double2float_rd(q), q2d = __double2float_rd(q2);
+      const float k2u = __double2float_ru(p.k2), Bu = __double2float_ru(B);
+      const float sgu = __double2float_ru(sig), Bsu = __fdiv_ru(Bu, __double2float_rd(sig));
+      const float c_dy = __fadd_ru(__fdiv_ru(__fmaf_ru(2.0f, k2u, kC8), q2d), 1.0f);
+      const float n_ty = __fadd_ru(kNty0, c_dy);
       // q < 0.01 (e > 0.99): the atan argument (below 1/q) leaves the range
       // over which kEpsAtanc is measured, and the bound is not finite
-      const double Gx = q < 0.01 ? 1e30 : gam(n_tx + kEpsAtanc + 3.5);
+      const bool flat = q < 0.01;
+      const float Gx = flat ? 1e30f : kGx;
       // 1/(q^2 - 3 n_ty u): the elasticity along the perturbed path
-      const double el = 1.0 / fmax(q2 - 3.0 * n_ty * U, 1e-300);
+      const float eld = __fsub_rd(q2d, __fmul_ru(3.0f * kU32, n_ty));
+      const float el = eld > 0.0f ? __frcp_ru(eld) : 1e30f;
       // atanh(t)/t: the polynomial's error, or the logarithm's divided by
       // 1 - t_y^2 >= q^2 - 3 n_ty u
-      const double eps_h = fmax(kEpsAtanhc, kEpsAtanhcLog * el);
-      const double Gy = q < 0.01 ? 1e30 : gam(n_ty * el + 0.5 * p.k2 * el + eps_h + 3.0);
+      const float eps_h = fmaxf(kEpsAtanhcF, __fmul_ru(kEpsAtanhcLogF, el));
+      const float Gy = flat || !(eld > 0.0f)
+                           ? 1e30f
+                           : gam_up(__fadd_ru(__fadd_ru(__fmaf_ru(n_ty, el, __fmul_ru(__fmul_ru(0.5f, k2u), el)),
+                                                        eps_h),
+                                              3.0f));
       // Input errors (rotated frame, 2-norm): |e'| <= sqrt(2) u (1+3u)
       // (W2 + 4.01 |Delta|_1), W2 <= 2 W.  The Jacobian of the dPIE in the
       // rotated frame, per unit B, is H_a - H_s with H_w positive
@@ -277,34 +325,49 @@ __global__ void __launch_bounds__(kPrepThreads)
       // factor; errP0 = 2 sqrt(2) B (1+3u) / (1 - (2 + eps_r) u), ra errs by
       // (2 + eps_r) u) and the |Delta| part Q = 16.04 B / q; otherwise P =
       // 28.36 B W max(1, x_k) covers all input errors (stage_p32).
-      const double p0 = 2.8285 * B * (1.0 + 3.0 * U) / (1.0 - (2.0 + kEpsRsqrt) * U);
-      f.f[4] = make_float4(__double2float_ru(p0), __double2float_ru(Gx * Bs),
-                           __double2float_ru(Gy * Bs), (float)(Bs * p.s));
-      Q = 16.04 * (1.0 + 3.0 * U) * B / q;
+      f.f[4] = make_float4(__fmul_ru(kP0Piemd, Bu), __fmul_ru(Gx, Bsu), __fmul_ru(Gy, Bsu),
+                           (float)(Bs * p.s));
+      Q = __fdiv_ru(__fmul_ru(kQPiemd, Bu), qd);
       // tight re-evaluation: the input errors are relative to the distance,
       // |e'| <= sqrt(2) 5.02 u (1+3u) |Delta|_1 <= 10.04 u (1+3u) |Delta|, and
       // psi_a >= q |Delta| along the segment (|e'| / psi_a <= 10.04 u / q is
       // negligible for q >= 0.01), so B |H|_2 |e'| <= 10.1 (1+3u) u B / q; the
       // evaluation terms stay per node (G)
-      Q2 = q < 0.01 ? 1e30 : 10.1 * (1.0 + 3.0 * U) * B / q;
+      Q2 = flat ? 1e30f : __fdiv_ru(__fmul_ru(kQ2Piemd, Bu), qd);
       // coarse bound: the largest |gx|, |gy| over the plane.  |g_x| =
       // |atan(A) - atan(B)| <= atan(sig/q) (0 <= B <= A < sig/q) and |g_y| <=
       // atanh(sig) (the two atanh arguments lie in (-sig, sig) with one sign),
-      // each times its evaluation factor 1 + G u.
-      const double mgx = atan(sig / q) * (1.0 + Gx * U);
-      const double mgy = atanh(fmin(sig, 1.0 - 1e-16)) * (1.0 + Gy * U);
-      Gmax = Bs * (Gx * mgx + Gy * mgy);
+      // each times its evaluation factor 1 + G u.  Both from the FP32
+      // functions whose errors are measured over every float argument:
+      // atan(x) = x atanc(x^2) <= x_up atanc_sq32(x_dn^2) (1 + (eps_atanc + 0.1) u)
+      // (atan(t)/t decreases in t^2), and atanh(s) = s atanhc(s^2) <= s_up
+      // atanhc_sq32(s_up^2) (1 + (eps + 0.1) u), eps the polynomial's error or the
+      // logarithm's divided by 1 - s^2 (atanh(t)/t increases in t^2).
+      const float xu = __fdiv_ru(sgu, qd);
+      const float xd = __fdiv_rd(__double2float_rd(sig), __double2float_ru(q));
+      const float atn = __fmul_ru(__fmul_ru(xu, atanc_sq32(fminf(__fmul_rd(xd, xd), 16384.0f))),
+                                  kAtanF);
+      const float s2 = fminf(__fmul_ru(sgu, sgu), 0.99999988f);
+      const float eh = s2 <= 0.25f ? kEpsAtanhcF : __fdiv_ru(kEpsAtanhcLogF, __fsub_rd(1.0f, s2));
+      const float atnh = __fmul_ru(__fmul_ru(fminf(sgu, 0.99999994f), atanhc_sq32(s2)),
+                                   __fmaf_ru(__fadd_ru(eh, 0.1f), kU32, 1.0f));
+      const float mgx = __fmul_ru(atn, __fmaf_ru(Gx, kU32, 1.0f));
+      const float mgy = __fmul_ru(atnh, __fmaf_ru(Gy, kU32, 1.0f));
+      Gmax = __fmul_ru(Bsu, __fmaf_ru(Gx, mgx, __fmul_ru(Gy, mgy)));
       // |t_x| + |t_y| <= (B/sig)(|c| + |s|)(|gx| + |gy|)(1 + u)
-      T = Bs * (fabs(p.c) + fabs(p.s)) * (mgx + mgy) * (1.0 + 2.0 * U);
+      T = __fmul_ru(__fmul_ru(__fmul_ru(Bsu, __double2float_ru(fabs(p.c) + fabs(p.s))),
+                              __fadd_ru(mgx, mgy)),
+                    kT2u);
     }
-    qsum = __fadd_ru(qsum, __double2float_ru(Q));
-    tsum = __fadd_ru(tsum, __double2float_ru(Q2));
+    qsum = __fadd_ru(qsum, Q);
+    tsum = __fadd_ru(tsum, Q2);
     // coarse bound: Q, the largest evaluation terms, and every accumulation
     // step's 2 (|PX| + |PY|) and flush's 2 (|AX| + |AY|) bounded by the
     // largest terms they can contain
     int w_partial, w_flush;
     sum_weights(rank, n_pot, cnt[LT_SIS], cnt[LT_PIEMD], &w_partial, &w_flush);
-    csum = __fadd_ru(csum, __double2float_ru(Q + Gmax + 2.0 * T * (w_partial + w_flush)));
+    csum = __fadd_ru(csum, __fadd_ru(__fadd_ru(Q, Gmax),
+                                     __fmul_ru(__fmul_ru(2.0f, T), (float)(w_partial + w_flush))));
     f.c64 = make_double2(p.cx, p.cy);
     pot32[(int64_t)b * n_pot + rank] = f;
   }

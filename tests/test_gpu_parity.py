@@ -464,6 +464,40 @@ def test_chi2_c4(oracle, prec):
     check_chi2(oracle, W.c4(), load_obs("c4"), prec)
 
 
+@pytest.mark.parametrize("prec", [lt.FP64, lt.MIXED])
+def test_chi2_invalid_system_is_latched(oracle, prec):
+    """A system with a negative D_ls/D_s (outside the input domain) gets no
+    predicted images: LT_ERR_NONFINITE is latched, its observed images take
+    the penalty (L_diag/sigma)^2 of an unlensed system, and every other
+    system's matches and chi^2 terms equal the oracle's."""
+    w = W.c4()
+    o = load_obs("c4")
+    bad = 3
+    ob = dict(o, dls_ds=[(-0.5 if s_ == bad else r_) for s_, r_ in enumerate(o["dls_ds"])])
+    m = lt.Model(w.n_pot, 1)
+    m.set_params(w.params)
+    grid = w.grids[0].as_tuple()
+    c2 = m.chi2([grid], lt.Observations.from_dict(ob), precision=prec)
+    st, _ = m.sync()
+    assert st == lt.LT_ERR_NONFINITE
+    mt, mxy, _ = m.last_matches(len(o["x"]), len(o["dls_ds"]))
+    c2, mt, mxy = float(c2.cpu().numpy()[0]), mt.cpu().numpy()[0], mxy.cpu().numpy()[0]
+    ref = oracle.chi2(w.params[0], grid, o, n_threads=4)
+    sys_ = np.asarray(o["sys"])
+    assert np.all(mt[sys_ == bad] < 0)
+    assert np.array_equal(mt[sys_ != bad], ref["match_tri"][sys_ != bad])
+    x, y, sig = np.asarray(o["x"]), np.asarray(o["y"]), np.asarray(o["sigma"])
+    res2 = (x - ref["match_xy"][:, 0]) ** 2 + (y - ref["match_xy"][:, 1]) ** 2
+    diag = math.hypot((grid[4] - 1) * grid[2], (grid[5] - 1) * grid[3])
+    pen = diag ** 2 / sig ** 2
+    term = np.where(ref["match_tri"] >= 0, res2 / sig ** 2, pen)
+    expect = float(np.sum(np.where(sys_ == bad, pen, term)))
+    tol = 1e-4 if prec == lt.MIXED else 1e-9
+    ok = (sys_ != bad) & (ref["match_tri"] >= 0)
+    ctol = np.sum((2 * np.sqrt(res2[ok]) * tol * 1.5 + 2 * tol * tol) / sig[ok] ** 2)
+    assert abs(c2 - expect) <= ctol + 1e-12 * expect, (c2, expect)
+
+
 def test_chi2_batched_uneven(oracle):
     """Eight perturbed samples on grids of uneven sizes in one call."""
     w = W.c3(batch=8)
