@@ -65,6 +65,13 @@ struct lt_model {
   SampleGrid* d_plan_grids = nullptr;
   int64_t* d_plan_items = nullptr;
   size_t plan_items_alloc = 0;
+  float* d_plan_coords = nullptr;  // FP32 node coordinates of every grid (SampleGrid::coord_off)
+  size_t plan_coords_alloc = 0;
+  // the coordinate table of the last single-grid deflection (lt_deflect_grid),
+  // uploaded again only when the grid changes
+  lt_grid dg_grid{};
+  float* d_dg_coords = nullptr;
+  size_t dg_coords_alloc = 0;
   // dynamic item counters: [0] single-grid calls, then (deflect, search) per chunk
   unsigned long long* d_sched = nullptr;
   size_t sched_alloc = 0;
@@ -198,7 +205,7 @@ bool same_grids(const std::vector<lt_grid>& a, const lt_grid* b, int n) {
 }
 
 // Device description of one sample's grid whose nodes start at node_off.
-SampleGrid sample_grid(const lt_grid& g, int64_t node_off) {
+SampleGrid sample_grid(const lt_grid& g, int64_t node_off, int64_t coord_off) {
   SampleGrid s;
   s.x0 = g.x0; s.y0 = g.y0; s.dx = g.dx; s.dy = g.dy; s.nx = g.nx; s.ny = g.ny;
   s.node_off = node_off;
@@ -207,7 +214,18 @@ SampleGrid sample_grid(const lt_grid& g, int64_t node_off) {
   s.theta_max = (float)(tm * (1.0 + 1e-6));
   s.pad = 0.f;
   s.x0f = (float)g.x0; s.y0f = (float)g.y0; s.dxf = (float)g.dx; s.dyf = (float)g.dy;
+  s.coord_off = coord_off;
   return s;
+}
+
+// Append a grid's FP32 node coordinates, nx values x0 + i dx then ny values
+// y0 + j dy: each evaluated in FP64 as written (this file is compiled without
+// floating-point contraction, so the product and the sum round separately, as
+// in an FP64 reference that states the grid the same way) and rounded once
+// to FP32.
+void grid_coords(const lt_grid& g, std::vector<float>& out) {
+  for (int i = 0; i < g.nx; ++i) out.push_back((float)(g.x0 + (double)i * g.dx));
+  for (int j = 0; j < g.ny; ++j) out.push_back((float)(g.y0 + (double)j * g.dy));
 }
 
 // Deflection work items of one grid: node ranges of kDefl64Nodes in FP64,
@@ -235,6 +253,7 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
   p.shape = shape;
   std::vector<SampleGrid> sg(n);
   std::vector<int64_t> items;
+  std::vector<float> coords;
   int b = 0;
   while (b < n) {
     Chunk c;
@@ -244,7 +263,8 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
       size_t nb = (size_t)grids[b].nx * grids[b].ny;
       if (b > c.b0 && nodes + nb > budget_nodes) break;
       const lt_grid& g = grids[b];
-      sg[b] = sample_grid(g, (int64_t)nodes);
+      sg[b] = sample_grid(g, (int64_t)nodes, (int64_t)coords.size());
+      grid_coords(g, coords);
       nodes += nb;
       ++b;
     }
@@ -275,6 +295,10 @@ lt_status make_plan(lt_model* m, const lt_grid* grids, int n, int precision, cud
   if (s != LT_OK) return s;
   s = grow(m, &m->d_sched, &m->sched_alloc, 1 + 2 * p.chunks.size());
   if (s != LT_OK) return s;
+  s = grow(m, &m->d_plan_coords, &m->plan_coords_alloc, coords.size());
+  if (s != LT_OK) return s;
+  LT_CUDA(cudaMemcpyAsync(m->d_plan_coords, coords.data(), sizeof(float) * coords.size(),
+                          cudaMemcpyHostToDevice, st));
   LT_CUDA(cudaMemcpyAsync(m->d_plan_grids, sg.data(), sizeof(SampleGrid) * n,
                           cudaMemcpyHostToDevice, st));
   LT_CUDA(cudaMemcpyAsync(m->d_plan_items, items.data(), sizeof(int64_t) * items.size(),
@@ -437,8 +461,8 @@ lt_status enqueue_search(lt_model* m, size_t ci, int precision, Sources src, int
       ProfScope ps(m, st, 0, np, 0);
       // the coarse bound: the resolution re-evaluates undecided nodes tightly
       LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)c.b0 * m->n_pot, m->d_seg + c.b0, m->n_pot,
-                               g, di, nb, c.defl_items, m->shape, false, nodes, next_defl,
-                               m->sm_count, st));
+                               g, m->d_plan_coords, di, nb, c.defl_items, m->shape, false, nodes,
+                               next_defl, m->sm_count, st));
     }
     if (wait_before_search) LT_CUDA(cudaStreamWaitEvent(st, wait_before_search, 0));
     {
@@ -597,7 +621,8 @@ void lt_model_destroy(lt_model* m) {
   cudaDeviceSynchronize();
   void* ptrs[] = {m->d_params, m->d_pot64, m->d_pot32, m->d_seg, m->d_status, m->d_counters,
                   m->d_nodes, m->d_hits, m->d_work, m->d_hit_count, m->d_work_count,
-                  m->d_plan_grids, m->d_plan_items, m->d_beta_obs, m->d_bary, m->d_match_tri,
+                  m->d_plan_grids, m->d_plan_items, m->d_plan_coords, m->d_dg_coords,
+                  m->d_beta_obs, m->d_bary, m->d_match_tri,
                   m->d_match_hit, m->d_match_xy, m->d_adj_lam, m->d_adj_pts, m->d_sched,
                   m->d_src_beta, m->d_src_mu, m->d_src_bary, m->d_chi2_terms, m->rs.keys,
                   m->rs.hval,
@@ -650,7 +675,7 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   cudaStream_t st = S(stream);
   // a one-sample plan over the caller's grid (does not disturb the batch plan)
   const lt_grid& g = *grid;
-  const SampleGrid sg = sample_grid(g, 0);
+  const SampleGrid sg = sample_grid(g, 0, 0);
   const int64_t nodes = (int64_t)g.nx * g.ny;
   LT_CHECK_ARG(precision != LT_PREC_PAPER || nodes < ((int64_t)1 << 31),
                "LT_PREC_PAPER grids are limited to 2^31 nodes");
@@ -665,9 +690,24 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   // node workspace layout: [float4 nodes][flags][int32 list][OneSample]; the
   // sample's plan lives after its nodes, so the batch plan's tables stay intact
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t node_bytes = precision == LT_PREC_FP64 ? 0 : up(sizeof(float4) * (size_t)nodes);
+  const bool fp32 = precision != LT_PREC_FP64;
+  const size_t node_bytes = fp32 ? up(sizeof(float4) * (size_t)nodes) : 0;
   const size_t flag_bytes = precision == LT_PREC_PAPER ? up((size_t)nodes) : 0;
   const size_t list_bytes = precision == LT_PREC_PAPER ? up(sizeof(int32_t) * (size_t)nodes) : 0;
+  if (fp32 && (!m->d_dg_coords || std::memcmp(&m->dg_grid, &g, sizeof(lt_grid)) != 0)) {
+    std::vector<float> coords;
+    grid_coords(g, coords);
+    if (m->dg_coords_alloc < coords.size()) {
+      if (m->d_dg_coords) LT_CUDA(cudaFree(m->d_dg_coords));
+      m->d_dg_coords = nullptr;
+      m->dg_coords_alloc = 0;
+      LT_CUDA(cudaMalloc(&m->d_dg_coords, sizeof(float) * coords.size()));
+      m->dg_coords_alloc = coords.size();
+    }
+    LT_CUDA(cudaMemcpyAsync(m->d_dg_coords, coords.data(), sizeof(float) * coords.size(),
+                            cudaMemcpyHostToDevice, st));
+    m->dg_grid = g;
+  }
   const size_t need = node_bytes + flag_bytes + list_bytes + up(sizeof(OneSample));
   lt_status s = ensure_nodes(m, need);
   if (s != LT_OK) return s;
@@ -691,8 +731,8 @@ lt_status lt_deflect_grid(lt_model* m, int32_t sample, const lt_grid* grid,
   // otherwise (its bound is not output; the deflection is the same)
   const bool tight = err_out != nullptr && precision == LT_PREC_MIXED;
   LT_CUDA(launch_deflect32(m->d_pot32 + (size_t)sample * m->n_pot, m->d_seg + sample, m->n_pot,
-                           &dev->g, dev->items, 1, items[1], m->shape, tight, nodes4, m->d_sched,
-                           m->sm_count, st));
+                           &dev->g, m->d_dg_coords, dev->items, 1, items[1], m->shape, tight,
+                           nodes4, m->d_sched, m->sm_count, st));
   if (precision == LT_PREC_MIXED) {
     LT_CUDA(launch_unpack32(nodes4, nodes, (float2*)alpha_out, err_out, st));
     return LT_OK;
@@ -968,11 +1008,14 @@ lt_status lt_autotune(lt_model* m, const lt_grid* grid, uintptr_t stream, int32_
   static_assert(sizeof(OneShape) % 8 == 0, "alignment");
   std::vector<OneShape> hs(kNumShapes);
   for (int v = 0; v < kNumShapes; ++v) {
-    hs[v] = OneShape{sample_grid(g, 0), {0, defl_items(g, LT_PREC_MIXED, v)}};
+    hs[v] = OneShape{sample_grid(g, 0, 0), {0, defl_items(g, LT_PREC_MIXED, v)}};
   }
+  std::vector<float> coords;
+  grid_coords(g, coords);
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t node_bytes = up(sizeof(float4) * (size_t)nodes);
-  lt_status s = ensure_nodes(m, node_bytes + up(sizeof(OneShape) * hs.size()));
+  const size_t plan_bytes = up(sizeof(OneShape) * hs.size());
+  lt_status s = ensure_nodes(m, node_bytes + plan_bytes + up(sizeof(float) * coords.size()));
   if (s != LT_OK) return s;
   if (!m->d_sched) {
     s = grow(m, &m->d_sched, &m->sched_alloc, 1);
@@ -980,8 +1023,11 @@ lt_status lt_autotune(lt_model* m, const lt_grid* grid, uintptr_t stream, int32_
   }
   char* base = (char*)m->d_nodes;
   OneShape* dplan = (OneShape*)(base + node_bytes);
+  float* dcoords = (float*)(base + node_bytes + plan_bytes);
   LT_CUDA(cudaMemcpyAsync(dplan, hs.data(), sizeof(OneShape) * hs.size(), cudaMemcpyHostToDevice,
                           st));
+  LT_CUDA(cudaMemcpyAsync(dcoords, coords.data(), sizeof(float) * coords.size(),
+                          cudaMemcpyHostToDevice, st));
   cudaEvent_t e0, e1;
   LT_CUDA(cudaEventCreate(&e0));
   LT_CUDA(cudaEventCreate(&e1));
@@ -993,9 +1039,9 @@ lt_status lt_autotune(lt_model* m, const lt_grid* grid, uintptr_t stream, int32_
     for (int r = 0; r <= kReps; ++r) {  // r = 0 warms up
       LT_CUDA(cudaMemsetAsync(m->d_sched, 0, sizeof(unsigned long long), st));
       LT_CUDA(cudaEventRecord(e0, st));
-      LT_CUDA(launch_deflect32(m->d_pot32, m->d_seg, m->n_pot, &dplan[v].g, dplan[v].items, 1,
-                               hs[v].items[1], v, false, (float4*)base, m->d_sched, m->sm_count,
-                               st));
+      LT_CUDA(launch_deflect32(m->d_pot32, m->d_seg, m->n_pot, &dplan[v].g, dcoords,
+                               dplan[v].items, 1, hs[v].items[1], v, false, (float4*)base,
+                               m->d_sched, m->sm_count, st));
       LT_CUDA(cudaEventRecord(e1, st));
       LT_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;

@@ -20,6 +20,7 @@ template <int NT, int NPT, int MINB, bool TIGHT>
 __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict__ pot32,
                                                   const Seg32* __restrict__ seg, int n_pot,
                                                   const SampleGrid* __restrict__ grids,
+                                                  const float* __restrict__ coords,
                                                   const int64_t* __restrict__ item_off,
                                                   int n_samples, int64_t n_items,
                                                   float4* __restrict__ node_out,
@@ -49,12 +50,14 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
     const int band = (int)(pc / g.nx);
     const int i = (int)(pc - (int64_t)band * g.nx);
     const int j0 = band * NPT;
-    // node coordinates rounded once from FP64: error u|theta| (App. A's
-    // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
-    const float X = (float)(g.x0 + (double)i * g.dx);
+    // node coordinates rounded once from FP64 (the grid's coordinate table):
+    // error u|theta| (App. A's stored-value model), not u|x0| as an FP32
+    // x0 + i*dx would give, and no FP64 instruction in the kernel
+    const float* cx = coords + g.coord_off;
+    const float X = cx[i];
     float Y[NPT], AX[NPT], AY[NPT], ER[NPT];
 #pragma unroll
-    for (int m = 0; m < NPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
+    for (int m = 0; m < NPT; ++m) Y[m] = cx[g.nx + min(j0 + m, g.ny - 1)];
     deflect32_nodes<NT, NPT, TIGHT>(pot32 + (int64_t)b * n_pot, n_pot, sg, g.theta_max, X, Y,
                                     sp, AX, AY, ER, staged != b);
     staged = b;
@@ -70,7 +73,8 @@ __global__ void __launch_bounds__(NT, MINB) k_deflect32(const Pot32* __restrict_
 
 template <int NT, int NPT, int MINB, bool TIGHT>
 static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int n_pot,
-                                      const SampleGrid* grids, const int64_t* item_off,
+                                      const SampleGrid* grids, const float* coords,
+                                      const int64_t* item_off,
                                       int n_samples, int64_t n_items, float4* node_out,
                                       unsigned long long* next_item, int sm_count,
                                       cudaStream_t st) {
@@ -82,44 +86,49 @@ static cudaError_t launch_deflect32_t(const Pot32* pot32, const Seg32* seg, int 
   if (blocks > n_items) blocks = n_items;
   if (blocks < 1) return cudaSuccess;
   return launch_pdl(k_deflect32<NT, NPT, MINB, TIGHT>, dim3((unsigned)blocks), dim3(NT), st,
-                    pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item);
+                    pot32, seg, n_pot, grids, coords, item_off, n_samples, n_items, node_out,
+                    next_item);
 }
 
 template <int V>
 static cudaError_t launch_shape(const Pot32* pot32, const Seg32* seg, int n_pot,
-                               const SampleGrid* grids, const int64_t* item_off, int n_samples,
+                               const SampleGrid* grids, const float* coords,
+                               const int64_t* item_off, int n_samples,
                                int64_t n_items, bool tight, float4* node_out,
                                unsigned long long* next_item, int sm_count, cudaStream_t st) {
   constexpr DeflectShape sh = deflect_shape(V);
   if (tight)
     return launch_deflect32_t<sh.threads, sh.npt, sh.min_blocks, true>(
-        pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item, sm_count, st);
+        pot32, seg, n_pot, grids, coords, item_off, n_samples, n_items, node_out, next_item,
+        sm_count, st);
   return launch_deflect32_t<sh.threads, sh.npt, sh.min_blocks, false>(
-      pot32, seg, n_pot, grids, item_off, n_samples, n_items, node_out, next_item, sm_count, st);
+      pot32, seg, n_pot, grids, coords, item_off, n_samples, n_items, node_out, next_item,
+      sm_count, st);
 }
 
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
-                             const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, bool tight, float4* node_out,
-                             unsigned long long* next_item, int sm_count, cudaStream_t st) {
+                             const SampleGrid* grids, const float* coords,
+                             const int64_t* item_off, int n_samples, int64_t n_items, int shape,
+                             bool tight, float4* node_out, unsigned long long* next_item,
+                             int sm_count, cudaStream_t st) {
   static_assert(kNumShapes == 8, "one case per launch shape");
   switch (shape) {
-    case 1: return launch_shape<1>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    case 2: return launch_shape<2>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    case 3: return launch_shape<3>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    case 4: return launch_shape<4>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    case 5: return launch_shape<5>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    case 6: return launch_shape<6>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    case 7: return launch_shape<7>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                   tight, node_out, next_item, sm_count, st);
-    default: return launch_shape<0>(pot32, seg, n_pot, grids, item_off, n_samples, n_items,
-                                    tight, node_out, next_item, sm_count, st);
+    case 1: return launch_shape<1>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    case 2: return launch_shape<2>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    case 3: return launch_shape<3>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    case 4: return launch_shape<4>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    case 5: return launch_shape<5>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    case 6: return launch_shape<6>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    case 7: return launch_shape<7>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                   n_items, tight, node_out, next_item, sm_count, st);
+    default: return launch_shape<0>(pot32, seg, n_pot, grids, coords, item_off, n_samples,
+                                    n_items, tight, node_out, next_item, sm_count, st);
   }
 }
 

@@ -367,6 +367,10 @@ struct SampleGrid {
   float theta_max;   // largest |coordinate| of any node
   float pad;
   float x0f, y0f, dxf, dyf;  // x0, y0, dx, dy rounded to FP32 (once, on the host)
+  // offset of this grid's node coordinates in the FP32 coordinate table:
+  // nx values x0 + i dx, then ny values y0 + j dy, each evaluated in FP64 as
+  // written (no fused multiply-add) and rounded once to FP32, on the host
+  int64_t coord_off;
 };
 
 // Work item of the FP64 stage: an ambiguous (triangle, source) pair or an
@@ -444,9 +448,10 @@ cudaError_t launch_prep(const double* params, int batch, int n_pot, Pot64* pot64
 // next_item: a zeroed device counter, taken by atomicAdd (dynamic items);
 // tight: the node bound in its tight form (else the coarse one)
 cudaError_t launch_deflect32(const Pot32* pot32, const Seg32* seg, int n_pot,
-                             const SampleGrid* grids, const int64_t* item_off, int n_samples,
-                             int64_t n_items, int shape, bool tight, float4* node_out,
-                             unsigned long long* next_item, int sm_count, cudaStream_t st);
+                             const SampleGrid* grids, const float* coords,
+                             const int64_t* item_off, int n_samples, int64_t n_items, int shape,
+                             bool tight, float4* node_out, unsigned long long* next_item,
+                             int sm_count, cudaStream_t st);
 cudaError_t launch_deflect64(const Pot64* pot64, int n_pot, const SampleGrid* grids,
                              const int64_t* item_off, int n_samples, int64_t n_items,
                              double2* node_out, int sm_count, cudaStream_t st);

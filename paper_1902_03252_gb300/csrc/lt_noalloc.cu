@@ -80,12 +80,15 @@ __global__ void __launch_bounds__(kNT, kMinBlocks)
     const int band = (int)(pc / g.nx);
     const int i = (int)(pc - (int64_t)band * g.nx);
     const int j0 = band * kNPT;
-    // node coordinates rounded once from FP64: error u|theta| (App. A's
-    // stored-value model), not u|x0| as an FP32 x0 + i*dx would give
-    const float X = (float)(g.x0 + (double)i * g.dx);
+    // node coordinates rounded once from FP64 x0 + i dx, the product and the
+    // sum rounded separately (the batched path's coordinate table holds the
+    // same values): error u|theta| (App. A's stored-value model), not u|x0|
+    // as an FP32 x0 + i*dx would give
+    const float X = (float)__dadd_rn(g.x0, __dmul_rn((double)i, g.dx));
     float Y[kNPT], AX[kNPT], AY[kNPT], ER[kNPT];
 #pragma unroll
-    for (int m = 0; m < kNPT; ++m) Y[m] = (float)(g.y0 + (double)min(j0 + m, g.ny - 1) * g.dy);
+    for (int m = 0; m < kNPT; ++m)
+      Y[m] = (float)__dadd_rn(g.y0, __dmul_rn((double)min(j0 + m, g.ny - 1), g.dy));
     // the batched kernel's body: the same operations in the same order
     deflect32_nodes<kNT, kNPT, true>(pot32, n_pot, sg, theta1, X, Y, sp, AX, AY, ER,
                                      item == blockIdx.x);
@@ -141,6 +144,7 @@ extern "C" lt_status lt_deflect_grid_noalloc(const double* params, int32_t n_pot
   g.theta_max = (float)(tm * (1.0 + 1e-6));
   g.pad = 0.f;
   g.x0f = (float)gr.x0; g.y0f = (float)gr.y0; g.dxf = (float)gr.dx; g.dyf = (float)gr.dy;
+  g.coord_off = 0;  // unused: this kernel forms its coordinates itself
   const int64_t n_items = defl32_items(gr.nx, gr.ny, kNT, kNPT);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deflect32_noalloc, kNT, 0) !=
