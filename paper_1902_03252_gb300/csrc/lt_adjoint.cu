@@ -96,8 +96,16 @@ __global__ void __launch_bounds__(kAdjVtxThreads)
 // h's position along the triangle's image-plane edges; other images get zero
 // points.  Pass 2, after a block barrier: every observed image of system i is
 // a barycentre point with coefficient -(r_i / n_i) sum over the system's
-// predicted images of lambda.
+// predicted images of lambda.  The matched-hit and system arrays are first
+// staged in shared memory (the loops over them would otherwise wait on one
+// global load per observed image), with per-system lists of the observed
+// images in index order, so the system sums issue one FP64 add per image of
+// the longest system rather than one per observed image (GB300's FP64 unit
+// takes ~80 cycles per warp instruction, whatever the active lanes).  Beyond
+// kAdjLamSmemInts the kernel reads the arrays from global memory and scans;
+// both sum in the same order.
 constexpr int kAdjLamThreads = 256;
+constexpr int kAdjLamSmemInts = 12000;  // 3 n_obs + n_sys + 1 ints (48 000 bytes)
 
 __global__ void __launch_bounds__(kAdjLamThreads)
     k_adj_lam(int batch, const Hit* __restrict__ hits, int64_t hit_cap, lt_obs obs,
@@ -105,10 +113,46 @@ __global__ void __launch_bounds__(kAdjLamThreads)
               AdjPt* __restrict__ pts, int P) {
   const int b = blockIdx.x;
   if (b >= batch) return;  // block-uniform
-  const int32_t* mh = match_hit + (int64_t)b * obs.n_obs;
+  const int n_obs = obs.n_obs, n_sys = obs.n_sys;
+  const int32_t* mh = match_hit + (int64_t)b * n_obs;
+  const int32_t* sy = obs.sys;
   AdjPt* pp = pts + (int64_t)b * P;
-  double2* lb = lam + (int64_t)b * obs.n_obs;
-  for (int m = threadIdx.x; m < obs.n_obs; m += kAdjLamThreads) {
+  double2* lb = lam + (int64_t)b * n_obs;
+  extern __shared__ int s_obs[];  // [n_obs] hits, [n_obs] systems, [n_sys + 1] starts, [n_obs] list
+  const bool staged = 3 * n_obs + n_sys + 1 <= kAdjLamSmemInts;
+  int* first = s_obs + 2 * n_obs;
+  int* idx = first + n_sys + 1;
+  if (staged) {
+    int* smh = s_obs;
+    int* ssy = s_obs + n_obs;
+    for (int k = threadIdx.x; k < n_obs; k += kAdjLamThreads) {
+      smh[k] = mh[k];
+      ssy[k] = sy[k];
+    }
+    for (int i = threadIdx.x; i <= n_sys; i += kAdjLamThreads) first[i] = 0;
+    __syncthreads();
+    mh = smh;
+    sy = ssy;
+    // (indices outside [0, n_sys) break the lt_obs contract; they are left
+    // out of the lists so that no shared-memory write leaves them)
+    for (int k = threadIdx.x; k < n_obs; k += kAdjLamThreads) {
+      const int i = sy[k];
+      if ((unsigned)i < (unsigned)n_sys) atomicAdd(&first[i + 1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < n_sys; ++i) first[i + 1] += first[i];
+    __syncthreads();
+    // image k's place in its system's list: the images of the system before it
+    for (int k = threadIdx.x; k < n_obs; k += kAdjLamThreads) {
+      const int i = sy[k];
+      if ((unsigned)i >= (unsigned)n_sys) continue;
+      int rank = 0;
+      for (int k2 = 0; k2 < k; ++k2) rank += sy[k2] == i;
+      idx[first[i] + rank] = k;
+    }
+  }
+  for (int m = threadIdx.x; m < n_obs; m += kAdjLamThreads) {
     const int h = mh[m];
     if (!adj_owner(mh, m, h)) {
       for (int v = 0; v < 3; ++v) pp[3 * m + v] = AdjPt{0.0, 0.0, 0.0, 0.0};
@@ -118,13 +162,13 @@ __global__ void __launch_bounds__(kAdjLamThreads)
     const Hit H = hits[(int64_t)b * hit_cap + h];
     // dchi^2/dx of this predicted image, over every observed image matched to it
     double Gx = 0.0, Gy = 0.0;
-    for (int k = m; k < obs.n_obs; ++k) {
+    for (int k = m; k < n_obs; ++k) {
       if (mh[k] != h) continue;
       const double s2 = obs.sigma[k] * obs.sigma[k];
       Gx += -2.0 * (obs.x[k] - H.x) / s2;
       Gy += -2.0 * (obs.y[k] - H.y) / s2;
     }
-    const double r = obs.dls_ds[obs.sys[m]];
+    const double r = obs.dls_ds[sy[m]];
     double TX[3], TY[3], BX[3], BY[3];
     for (int v = 0; v < 3; ++v) {
       const AdjPt q = pp[3 * m + v];
@@ -145,18 +189,27 @@ __global__ void __launch_bounds__(kAdjLamThreads)
       pp[3 * m + v] = AdjPt{TX[v], TY[v], r * H.w[v] * lx, r * H.w[v] * ly};
   }
   __syncthreads();  // every lambda of the sample is written
-  for (int m = threadIdx.x; m < obs.n_obs; m += kAdjLamThreads) {
-    const int i = obs.sys[m];
+  for (int m = threadIdx.x; m < n_obs; m += kAdjLamThreads) {
+    const int i = sy[m];
     double Lx = 0.0, Ly = 0.0;
     int n = 0;
-    for (int k = 0; k < obs.n_obs; ++k) {
-      if (obs.sys[k] != i) continue;
-      ++n;
-      Lx += lb[k].x;
-      Ly += lb[k].y;
+    if (staged && (unsigned)i < (unsigned)n_sys) {
+      for (int j = first[i]; j < first[i + 1]; ++j) {
+        const double2 v = lb[idx[j]];
+        ++n;
+        Lx += v.x;
+        Ly += v.y;
+      }
+    } else {
+      for (int k = 0; k < n_obs; ++k) {
+        if (sy[k] != i) continue;
+        ++n;
+        Lx += lb[k].x;
+        Ly += lb[k].y;
+      }
     }
     const double fct = -obs.dls_ds[i] / n;
-    pp[3 * obs.n_obs + m] = AdjPt{obs.x[m], obs.y[m], fct * Lx, fct * Ly};
+    pp[3 * n_obs + m] = AdjPt{obs.x[m], obs.y[m], fct * Lx, fct * Ly};
   }
 }
 
@@ -346,8 +399,10 @@ cudaError_t launch_adjoint(const Pot64* pot64, int n_pot, int batch, const Sampl
                                                           hit_cap, obs, match_hit, pts, P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_adj_lam<<<(unsigned)batch, kAdjLamThreads, 0, st>>>(batch, hits, hit_cap, obs, match_hit,
-                                                        lam, pts, P);
+  const int nl = 3 * obs.n_obs + obs.n_sys + 1;
+  const size_t lam_smem = nl <= kAdjLamSmemInts ? sizeof(int) * (size_t)nl : 0;
+  k_adj_lam<<<(unsigned)batch, kAdjLamThreads, lam_smem, st>>>(batch, hits, hit_cap, obs,
+                                                               match_hit, lam, pts, P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t gblocks = (int64_t)batch * n_pot;
