@@ -236,6 +236,32 @@ def test_deflect_every_shape_within_bound(oracle, shape):
     np.testing.assert_array_equal(e, e1.cpu().numpy().astype(np.float64))
 
 
+def test_deflect_grids_in_turn_match_fresh_models():
+    """The single-grid path keeps the FP32 node-coordinate table of its last
+    grid: alternating grids (different origin, spacing and shape) must give
+    bit for bit what a fresh model gives for each."""
+    p = mixed_cluster(31, n_pot=25)
+    grids = [(-30.0, -30.0, 60.0 / 199, 60.0 / 199, 200, 200),
+             (-29.0, -31.0, 0.25, 0.3, 237, 181),
+             (-30.0, -30.0, 60.0 / 199, 60.0 / 199, 200, 200)]
+    fresh = []
+    for g in grids[:2]:
+        m = lt.Model(p.shape[1], 1)
+        m.set_params(p[None])
+        a, e = m.deflect_grid(g, precision=lt.MIXED, with_error=True)
+        fresh.append((a.cpu().numpy(), e.cpu().numpy()))
+        m.close()
+    m = lt.Model(p.shape[1], 1)
+    m.set_params(p[None])
+    for k, g in enumerate(grids):
+        a, e = m.deflect_grid(g, precision=lt.MIXED, with_error=True)
+        ref = fresh[0 if k != 1 else 1]
+        np.testing.assert_array_equal(a.cpu().numpy(), ref[0])
+        np.testing.assert_array_equal(e.cpu().numpy(), ref[1])
+    assert m.sync()[0] == lt.LT_OK
+    m.close()
+
+
 def test_deflect_c2_full_size_sampled(oracle):
     """The 2000^2, 100-PIEMD grid in the benchmark's launch configuration:
     every node within its bound on a sampled subset, FP64 on the same subset."""
