@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "lt_internal.cuh"
+#include "lt_source.cuh"
 
 namespace lt {
 
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(kSearch64Threads)
       const double Px = sxy[2 * k], Py = sxy[2 * k + 1], r = sr[k];
       // the mixed path's input domain: a finite position and 0 <= r < 1e30;
       // anything else is latched and the source has no images
-      if (!(isfinite(Px) && isfinite(Py) && r >= 0.0 && r < 1e30)) {
+      if (!source_ok(Px, Py, r)) {
         if (threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
         continue;
       }

@@ -7,6 +7,7 @@
 
 #include "lt_internal.cuh"
 #include "lt_fp32.cuh"
+#include "lt_source.cuh"
 
 namespace lt {
 
@@ -307,8 +308,10 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchBlocksPerSM)
           const double pxd = sxy[2 * (s0 + v)], pyd = sxy[2 * (s0 + v) + 1], rd = sr[s0 + v];
           // searched only with a finite position and a ratio 0 <= r < 1e30
           // (Eq. 13); otherwise latched, and the NaN ratio fails every
-          // comparison of the cull, so the source has no images
-          const bool ok = isfinite(pxd) && isfinite(pyd) && rd >= 0.0 && rd < 1e30;
+          // comparison of the cull, so the source has no images.  Tested on
+          // the bits (lt_source.cuh: every warp stages at once, and FP64
+          // compares would queue on the FP64 unit).
+          const bool ok = source_ok(pxd, pyd, rd);
           if (!ok) atomicOr(status, ST_NONFINITE);
           const float px = (float)pxd, py = (float)pyd;
           ss[v] = SrcSmem{px, py, ok ? (float)rd : __int_as_float(0x7fffffff),
